@@ -1,0 +1,84 @@
+/*
+ * FP64 CPU ORACLE for Path-Dependent Shapley values and pairwise Shapley
+ * interaction values of tree ensembles.  TEST INFRASTRUCTURE ONLY: the tests,
+ * the smoke check and the CPU-baseline leg of the benchmark call it; the
+ * product path never does.  It shares no code with the CUDA library.
+ *
+ * Contents (paper sections and equations cited at each definition):
+ *   orc_gl_nodes        Gauss-Legendre nodes/weights on [0,1] (Sec. 4, Sec. 6).
+ *   orc_predict         plain tree prediction f(x) (Sec. 2).
+ *   orc_shap_exact      phi_i by the exact integral of the Thm 1 polynomial
+ *                       (Eq. ao_shap_is_intergral..., Beta identity, App. C).
+ *   orc_sii_exact       pairwise SII_ij the same way (Thm 1 with |S|=2).
+ *   orc_shap_quad       phi_i with n-point Gauss-Legendre instead of the exact
+ *                       integral (Eq. shap_as_weighted_banzhafs).
+ *   orc_brute_force     phi_i and SII_ij by subset enumeration of the
+ *                       Path-Dependent game (Eq. path_dependent_game, App. C).
+ *   orc_alg1            Algorithm 1 (DFS with telescoping, orders 1 and 2).
+ *   orc_grad_exact      d(sum grad_phi*phi)/d(leaf values) and /d(edge weights),
+ *                       differentiating Thm 1 analytically (no paper passage;
+ *                       pinned by finite differences of the brute force).
+ *
+ * Parity pins live in tests/test_oracle_*.py; every function above is pinned.
+ */
+#ifndef QTS_ORACLE_H
+#define QTS_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Tree ensemble as node arrays; node indices are local to each tree, the root
+ * of tree t is node_offsets[t].  left/right = -1 at leaves.  z[n] is the edge
+ * weight w_e = n_child/n_parent of the edge into n (Sec. 2). */
+typedef struct orc_ens {
+    int32_t n_trees;
+    int32_t n_features;
+    const int64_t *node_offsets;
+    const int32_t *left;
+    const int32_t *right;
+    const int32_t *feature;
+    const float *threshold;
+    const uint8_t *default_left;
+    const float *z;
+    const float *leaf_value;
+} orc_ens;
+
+int orc_gl_nodes(int n, double *t, double *w);
+
+void orc_predict(const orc_ens *e, const float *X, int64_t M, double *out);
+
+/* phi: M x (F+1), last column E[f] = sum_v R_empty^v. */
+int orc_shap_exact(const orc_ens *e, const float *X, int64_t M, int n_threads, double *phi);
+
+/* sii: M x F x F symmetric with zero diagonal (the Shapley interaction index,
+ * not halved); phi may be NULL, else filled like orc_shap_exact. */
+int orc_sii_exact(const orc_ens *e, const float *X, int64_t M, int n_threads, double *sii,
+                  double *phi);
+
+/* phi with the integral replaced by n Gauss-Legendre points on [0,1]. */
+int orc_shap_quad(const orc_ens *e, const float *X, int64_t M, int n, int n_threads, double *phi);
+
+/* One sample; needs n_features <= 20.  phi: F+1, sii: F x F (may be NULL). */
+int orc_brute_force(const orc_ens *e, const float *x, double *phi, double *sii);
+
+/* Algorithm 1 on one sample with n Gauss-Legendre points; order 1 fills phi
+ * (F+1 incl. E[f]), order 2 fills sii (F x F, symmetric, zero diagonal). */
+int orc_alg1(const orc_ens *e, const float *x, int order, int n, double *out);
+
+/* L = sum_s sum_{f<=F} grad_phi[s,f] * phi[s,f].  Writes dL/d leaf_value and
+ * dL/d z for every node (N = node_offsets[n_trees]).  If leaves != NULL only
+ * the n_leaves listed leaves (global node indices) contribute, which gives
+ * exact values at those leaves' own nodes (d_leaf[v], d_z[v]). */
+int orc_grad_exact(const orc_ens *e, const float *X, int64_t M, const float *grad_phi,
+                   const int64_t *leaves, int64_t n_leaves, int n_threads, double *d_leaf,
+                   double *d_z);
+
+/* Merged-path summary for tests: number of paths and max unique features. */
+int orc_path_stats(const orc_ens *e, int64_t *n_paths, int32_t *max_d, int64_t *sum_d);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

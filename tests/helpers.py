@@ -1,0 +1,39 @@
+"""Shared test helpers: tiny ensembles (hand-written or seeded) and error norms."""
+import json
+import os
+
+import numpy as np
+
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden_trees():
+    with open(os.path.join(GOLDEN, "hand_trees.json")) as fh:
+        data = json.load(fh)
+    out = []
+    for t in data["trees"]:
+        n = len(t["left"])
+        ens = synth.Ensemble([0, n], t["left"], t["right"], t["feature"], t["threshold"],
+                             t["default_left"], t["z"], t["leaf_value"], np.zeros(n), t["n_features"])
+        out.append((t, ens))
+    return out
+
+
+def sample_x(s):
+    return np.array([np.nan if v == "nan" else v for v in s["x"]], dtype=np.float32)
+
+
+def tiny_ensemble(seed, n_trees=3, depth=5, F=6, n_train=200, full=False):
+    """Seeded random-split ensemble; depth > F forces repeated features."""
+    return synth.grow(seed, n_trees, depth, F, n_train, 1.0, min_rows=2, full_depth=full)
+
+
+def rel_err_rows(phi, ref):
+    """Per-sample error normalised by max(|f(x)|, max_i |phi_i|) of the reference:
+    |f(x)| alone is fragile when the prediction is near zero."""
+    fx = np.abs(ref.sum(axis=1))
+    scale = np.maximum(fx, np.abs(ref[:, :-1]).max(axis=1))
+    scale = np.maximum(scale, 1e-30)
+    return np.abs(phi - ref).max(axis=1) / scale

@@ -1,0 +1,287 @@
+"""Pins of the FP64 oracle against facts the paper and mathematics fix.
+
+Each test pins one oracle function to something other than itself: hand-derived
+values (tests/golden), closed forms, the Shapley axioms, a library quadrature
+routine, brute-force subset enumeration, or finite differences.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import golden_trees, rel_err_rows, sample_x, tiny_ensemble
+
+
+# ------------------------------------------------------------ Gauss-Legendre
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 12, 16, 24, 32])
+def test_gl_exact_on_monomials(n):
+    """n-point Gauss-Legendre integrates t^k exactly for k <= 2n-1 (Sec. 4, Thm 2)."""
+    t, w = oracle.gl_nodes(n)
+    assert np.all(np.diff(t) > 0) and t[0] > 0 and t[-1] < 1
+    assert abs(w.sum() - 1.0) < 1e-14
+    for k in range(2 * n):
+        assert abs((w * t**k).sum() - 1.0 / (k + 1)) < 1e-14, k
+    # degree 2n: the rule's remainder for t^(2n) on [0,1] is (n!)^4 / ((2n+1) ((2n)!)^2)
+    if n <= 8:
+        rem = math.factorial(n) ** 4 / ((2 * n + 1) * math.factorial(2 * n) ** 2)
+        got = 1.0 / (2 * n + 1) - (w * t ** (2 * n)).sum()
+        assert abs(got - rem) < 1e-9 * rem + 1e-16, (got, rem)
+
+
+@pytest.mark.parametrize("n", [1, 4, 8, 20])
+def test_gl_matches_numpy_leggauss(n):
+    """Same nodes as numpy's independent Golub-Welsch implementation, mapped to [0,1]."""
+    x, wx = np.polynomial.legendre.leggauss(n)
+    t, w = oracle.gl_nodes(n)
+    assert np.allclose(t, (x + 1) / 2, atol=1e-14)
+    assert np.allclose(w, wx / 2, atol=1e-14)
+
+
+def test_gl_closed_forms():
+    t, w = oracle.gl_nodes(1)
+    assert t[0] == 0.5 and w[0] == 1.0
+    t, w = oracle.gl_nodes(2)
+    r = 1 / (2 * math.sqrt(3))
+    assert np.allclose(t, [0.5 - r, 0.5 + r], atol=1e-15) and np.allclose(w, [0.5, 0.5], atol=1e-15)
+
+
+# ------------------------------------------------------------ hand-derived
+
+def test_golden_hand_trees():
+    """Every formulation reproduces the values derived by hand in tests/golden."""
+    for spec, ens in golden_trees():
+        for s in spec["samples"]:
+            x = sample_x(s)
+            want = np.array(s["phi"])
+            bf_phi, bf_sii = oracle.brute_force(ens, x)
+            ex = oracle.shap_exact(ens, x[None])[0]
+            a1 = oracle.alg1(ens, x, 1, 8)
+            sii, _ = oracle.sii_exact(ens, x[None])
+            a2 = oracle.alg1(ens, x, 2, 8)
+            for got in (bf_phi, ex, a1):
+                assert np.allclose(got, want, atol=1e-15, rtol=0), (spec["name"], got, want)
+            for got in (bf_sii[0, 1], sii[0, 0, 1], a2[0, 1]):
+                assert abs(got - s["sii01"]) < 1e-15, (spec["name"], got)
+            assert abs(oracle.predict(ens, x[None])[0] - s["fx"]) == 0
+
+
+def test_stump_closed_form():
+    """Single split on feature i: phi_i = val_taken - (w_l val_l + w_r val_r), others 0."""
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        F = 5
+        i = int(rng.integers(F))
+        cl, cr = rng.integers(1, 100, size=2)
+        vl, vr = rng.standard_normal(2).astype(np.float32)
+        thr = np.float32(rng.standard_normal())
+        zl, zr = np.float32(cl / (cl + cr)), np.float32(cr / (cl + cr))
+        ens = synth.Ensemble([0, 3], [1, -1, -1], [2, -1, -1], [i, -1, -1], [thr, 0, 0], [0, 0, 0],
+                             [1, zl, zr], [0, vl, vr], [0, 0, 0], F)
+        x = rng.standard_normal(F).astype(np.float32)
+        taken = vl if x[i] < thr else vr
+        ef = float(zl) * float(vl) + float(zr) * float(vr)
+        phi = oracle.shap_exact(ens, x[None])[0]
+        want = np.zeros(F + 1)
+        want[i] = float(taken) - ef
+        want[F] = ef
+        assert np.allclose(phi, want, atol=1e-15)
+
+
+# ------------------------------------------------------------ brute force
+
+@pytest.mark.parametrize("seed", range(12))
+def test_exact_equals_brute_force(seed):
+    """Exact Bernstein expansion of Thm 1 == subset enumeration of the game,
+    including repeated features on a path (depth 7 > F = 5)."""
+    ens = tiny_ensemble(1000 + seed, n_trees=3, depth=7, F=5)
+    X = synth.normal(77 + seed, 1, (4, 5))
+    phi = oracle.shap_exact(ens, X)
+    sii, _ = oracle.sii_exact(ens, X)
+    for s in range(X.shape[0]):
+        bf_phi, bf_sii = oracle.brute_force(ens, X[s])
+        scale = max(1.0, np.abs(bf_phi).max())
+        assert np.abs(phi[s] - bf_phi).max() < 1e-12 * scale
+        assert np.abs(sii[s] - bf_sii).max() < 1e-12 * scale
+
+
+def test_null_player_and_player_count():
+    """Adding never-split features leaves phi unchanged and gives them exactly
+    zero (Sec. 2 null player; Lemma 2 case 1) -- brute force over F and F+3."""
+    ens = tiny_ensemble(5, n_trees=2, depth=4, F=4)
+    X = synth.normal(5, 2, (3, 4))
+    big = ens.copy()
+    big.n_features = 7
+    Xb = np.concatenate([X, synth.normal(5, 3, (3, 3))], axis=1)
+    for s in range(3):
+        a, _ = oracle.brute_force(ens, X[s])
+        b, _ = oracle.brute_force(big, Xb[s])
+        assert np.allclose(a[:4], b[:4], atol=1e-13)
+        assert np.abs(b[4:7]).max() < 1e-13
+        assert abs(a[4] - b[7]) < 1e-13
+        c = oracle.shap_exact(big, Xb[s:s + 1])[0]
+        assert np.all(c[4:7] == 0.0)
+
+
+# ------------------------------------------------------------ axioms
+
+def test_efficiency_local_accuracy():
+    """sum_i phi_i + E[f] = f(x) (the paper's accuracy metric, Sec. 8)."""
+    w = synth.single_config(0)
+    phi = oracle.shap_exact(w.ens, w.X)
+    f = oracle.predict(w.ens, w.X)
+    assert np.abs(phi.sum(axis=1) - f).max() < 1e-12
+    sub = synth.single_config(1, n_samples=20, n_trees=20)
+    phi = oracle.shap_exact(sub.ens, sub.X)
+    f = oracle.predict(sub.ens, sub.X)
+    assert np.abs(phi.sum(axis=1) - f).max() < 1e-12
+
+
+def test_symmetry_under_feature_relabelling():
+    ens = tiny_ensemble(11, n_trees=3, depth=5, F=6)
+    X = synth.normal(11, 1, (5, 6))
+    perm = np.array([3, 0, 5, 1, 4, 2])  # new label of old feature k is perm[k]
+    rel = ens.copy()
+    rel.feature = np.where(ens.feature >= 0, perm[np.maximum(ens.feature, 0)], -1).astype(np.int32)
+    Xr = np.empty_like(X)
+    Xr[:, perm] = X
+    a = oracle.shap_exact(ens, X)
+    b = oracle.shap_exact(rel, Xr)
+    assert np.allclose(b[:, perm], a[:, :6], atol=1e-14)
+    assert np.allclose(a[:, 6], b[:, 6], atol=1e-14)
+
+
+def test_linearity_in_trees_and_leaf_values():
+    ens = tiny_ensemble(21, n_trees=4, depth=5, F=6)
+    X = synth.normal(21, 1, (6, 6))
+    whole = oracle.shap_exact(ens, X)
+    parts = sum(oracle.shap_exact(ens.tree(t), X) for t in range(ens.n_trees))
+    assert np.allclose(whole, parts, atol=1e-13)
+    scaled = ens.copy()
+    scaled.leaf_value = (ens.leaf_value * np.float32(2.0)).astype(np.float32)
+    assert np.allclose(oracle.shap_exact(scaled, X), 2.0 * whole, atol=1e-13)
+
+
+def test_missing_values_follow_default_direction():
+    ens = tiny_ensemble(31, n_trees=3, depth=5, F=5)
+    X = synth.normal(31, 1, (6, 5))
+    X[0, 1] = np.nan
+    X[1, :] = np.nan
+    X[2, 3] = np.nan
+    phi = oracle.shap_exact(ens, X)
+    f = oracle.predict(ens, X)
+    assert np.abs(phi.sum(axis=1) - f).max() < 1e-12
+    for s in range(3):
+        bf, _ = oracle.brute_force(ens, X[s])
+        assert np.allclose(phi[s], bf, atol=1e-12)
+
+
+# ------------------------------------------------------------ interactions
+
+def test_interaction_matrix_properties():
+    """Rows of the pred_interactions layout sum to phi_i; the whole matrix sums
+    to f(x); off-diagonal entries are SII/2 and symmetric."""
+    w = synth.single_config(3, n_samples=8, n_trees=10)
+    sii, phi = oracle.sii_exact(w.ens, w.X)
+    mat = oracle.interaction_matrix(sii, phi)
+    F = w.F
+    assert np.allclose(mat[:, :F, :F].sum(axis=2), phi[:, :F], atol=1e-13)
+    assert np.allclose(mat.sum(axis=(1, 2)), oracle.predict(w.ens, w.X), atol=1e-12)
+    assert np.allclose(mat, np.transpose(mat, (0, 2, 1)), atol=0)
+
+
+# ------------------------------------------------------------ Algorithm 1 / Thm 2
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_alg1_exact_at_theorem2_bound(order):
+    """Alg. 1 with n = ceil((d - s + 1)/2) points is exact (Thm 2)."""
+    ens = tiny_ensemble(41, n_trees=3, depth=9, F=9, n_train=2000)
+    _, dmax, _ = oracle.path_stats(ens)
+    X = synth.normal(41, 1, (3, 9))
+    n = math.ceil((dmax - order + 1) / 2)
+    for s in range(3):
+        if order == 1:
+            ref = oracle.shap_exact(ens, X[s:s + 1])[0]
+        else:
+            ref = oracle.sii_exact(ens, X[s:s + 1], with_phi=False)[0][0]
+        got = oracle.alg1(ens, X[s], order, n)
+        scale = max(1.0, np.abs(ref).max())
+        assert np.abs(got - ref).max() < 1e-12 * scale
+
+
+def test_quadrature_exact_iff_degree_covered():
+    """n-point quadrature equals the exact integral for paths with d <= 2n
+    unique features (integrand degree d - 1 <= 2n - 1), and misses it once d
+    exceeds 2n."""
+    ens = tiny_ensemble(51, n_trees=4, depth=10, F=10, n_train=4000)
+    _, dmax, _ = oracle.path_stats(ens)
+    assert dmax >= 8
+    X = synth.normal(51, 1, (4, 10))
+    ref = oracle.shap_exact(ens, X)
+    ok = oracle.shap_quad(ens, X, math.ceil(dmax / 2))
+    assert np.abs(ok - ref).max() < 1e-12 * max(1.0, np.abs(ref).max())
+    low = oracle.shap_quad(ens, X, 2)
+    assert np.abs(low - ref).max() > 1e-9
+
+
+def test_eight_points_exact_on_depth8_config():
+    sub = synth.single_config(1, n_samples=10, n_trees=30)
+    ref = oracle.shap_exact(sub.ens, sub.X)
+    q = oracle.shap_quad(sub.ens, sub.X, 8)
+    assert rel_err_rows(q, ref).max() < 1e-13
+
+
+# ------------------------------------------------------------ gradients
+
+def _loss_brute(ens, X, G):
+    tot = 0.0
+    for s in range(X.shape[0]):
+        phi, _ = oracle.brute_force(ens, X[s])
+        tot += float((G[s].astype(np.float64) * phi).sum())
+    return tot
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_gradient_matches_finite_differences_of_brute_force(seed):
+    """phi is linear in every leaf value and every single edge weight, so a
+    central difference of the brute-force game is exact up to rounding."""
+    ens = tiny_ensemble(61 + seed, n_trees=2, depth=5, F=4, n_train=100)
+    X = synth.normal(61 + seed, 1, (5, 4))
+    G = synth.normal(61 + seed, 2, (5, 5))
+    d_leaf, d_z = oracle.grad_exact(ens, X, G)
+    roots = set(int(o) for o in ens.node_offsets[:-1])
+    for n in range(ens.n_nodes):
+        for name, g in (("leaf_value", d_leaf), ("z", d_z)):
+            if name == "leaf_value" and ens.left[n] >= 0:
+                assert g[n] == 0.0
+                continue
+            if name == "z" and n in roots:
+                continue
+            h = 1.0 if name == "leaf_value" else 1e-2
+            ep, em = ens.copy(), ens.copy()
+            getattr(ep, name)[n] += np.float32(h)
+            getattr(em, name)[n] -= np.float32(h)
+            hp = float(getattr(ep, name)[n]) - float(getattr(em, name)[n])
+            fd = (_loss_brute(ep, X, G) - _loss_brute(em, X, G)) / hp
+            assert abs(fd - g[n]) <= 1e-10 * max(1.0, abs(g[n])), (name, n, fd, g[n])
+
+
+def test_gradient_leaf_subset_is_exact_at_listed_leaves():
+    ens = tiny_ensemble(71, n_trees=3, depth=5, F=5)
+    X = synth.normal(71, 1, (7, 5))
+    G = synth.normal(71, 2, (7, 6))
+    full_l, full_z = oracle.grad_exact(ens, X, G)
+    leaves = np.flatnonzero(ens.left < 0)[::3]
+    # global leaf index -> local within tree: grad_exact takes global node indices
+    sub_l, sub_z = oracle.grad_exact(ens, X, G, leaves=leaves)
+    assert np.allclose(sub_l[leaves], full_l[leaves], atol=1e-13)
+    assert np.allclose(sub_z[leaves], full_z[leaves], atol=1e-13)
+
+
+def test_threads_do_not_change_results():
+    w = synth.single_config(0)
+    a = oracle.shap_exact(w.ens, w.X, n_threads=1)
+    b = oracle.shap_exact(w.ens, w.X, n_threads=7)
+    assert np.array_equal(a, b)
