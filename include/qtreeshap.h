@@ -1,0 +1,227 @@
+/*
+ * qtreeshap.h - C ABI of the GB300 (sm_103a) Quadrature-TreeSHAP library.
+ *
+ * What it computes (arXiv 2605.04497):
+ *   For a tree ensemble with edge weights w_e = n_child/n_parent (Sec. 2) and a
+ *   sample x, the Path-Dependent Shapley value of feature i is
+ *       phi_i = sum_v val(v) (o_i - z_i) int_0^1 prod_{j != i} a_j(p) dp
+ *   and the pairwise Shapley interaction index of features i != j is
+ *       SII_ij = sum_v val(v) (o_i - z_i)(o_j - z_j) int_0^1 prod_{k != i,j} a_k(p) dp,
+ *   where the sum runs over leaves v whose root-to-leaf path uses the features,
+ *   the path's splits are merged per feature (Eq. q_def), z_j is the product of
+ *   the path's edge weights on feature j, o_j = 1 if x satisfies all of the
+ *   path's splits on j, and a_j(p) = (1-p) z_j + p o_j.  This is Thm 1 with
+ *   S = {i} and S = {i,j} (Eq. weighted_banzhaf_iv_v2 with R_empty = val prod w,
+ *   q_j = o_j/z_j) integrated over p as in Eq. ao_shap_is_intergral_of_ao_banzhaf.
+ *   The integral is evaluated with n_quad Gauss-Legendre points on [0,1]
+ *   (Eq. shap_as_weighted_banzhafs; Sec. 6 fixes n = 8), which is exact when
+ *   the path has at most 2*n_quad unique features (Thm 2).
+ *
+ * Conventions (all entry points):
+ *   - Device pointers are CUDA device memory of the current device; they are
+ *     owned by the caller and must stay valid until the stream work completes.
+ *     Host pointers are read during the call only.
+ *   - Every compute call is asynchronous on `stream` and only enqueues work.
+ *     Argument errors are reported synchronously by the return code; faults
+ *     detected on the device (a bounded wait that ran out) are latched in the
+ *     ensemble's device status word and reported by qts_sync_status.
+ *   - Nothing ever aborts or traps; on error the return code is non-zero and
+ *     qts_last_error() describes it (thread-local string).
+ *   - Calls that use the same ensemble must not overlap on the GPU (they share
+ *     the ensemble's workspace); enqueue them on one stream.
+ *   - X is M x F row-major fp32 with F equal to the ensemble's n_features.
+ *     x[f] < threshold goes left, x[f] >= threshold right, NaN goes the node's
+ *     default direction.
+ */
+#ifndef QTREESHAP_H
+#define QTREESHAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *qts_stream_t; /* same handle as cudaStream_t; NULL = legacy default */
+
+typedef struct qts_ensemble qts_ensemble; /* opaque; owns the device path tables */
+
+typedef enum qts_status {
+    QTS_OK = 0,
+    QTS_ERR_ARG = 1,          /* invalid argument (pointer, size, topology) */
+    QTS_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+    QTS_ERR_OOM = 3,          /* device or host allocation failed */
+    QTS_ERR_UNSUPPORTED = 4,  /* valid input outside the supported envelope */
+    QTS_ERR_TIMEOUT = 5,      /* a bounded device wait ran out (reported by qts_sync_status) */
+    QTS_ERR_DEVICE_CHECK = 6  /* a device-side consistency check failed */
+} qts_status;
+
+/* flags for qts_load_ensemble */
+#define QTS_FLAG_FP64 1u /* all path arithmetic in FP64 (correctness mode, slow on GB300) */
+
+/* Limits of the supported envelope. */
+#define QTS_MAX_UNIQUE_FEATURES_PER_PATH 64
+#define QTS_MAX_FEATURES 640 /* sample and accumulator tiles live in shared memory */
+#define QTS_MAX_QUAD 32
+
+/*
+ * qts_load_ensemble - copy a tree ensemble and build its path tables.
+ * Sec. 2 (edge weights, Eq. R_empty, Eq. q_def): every root-to-leaf path is
+ * enumerated, splits on the same feature are merged into one element
+ * (z = product of their edge weights, the interval [lo, hi) satisfying them all,
+ * and whether NaN satisfies them all), paths are bucketed by unique-feature
+ * count and uploaded as structure-of-arrays tables.
+ *
+ *   n_trees            number of trees (>= 1)
+ *   tree_node_offsets  host, n_trees+1 ascending; tree t owns nodes
+ *                      [off[t], off[t+1]); its root is local node 0
+ *   left, right        host, local child indices within the tree, -1 at leaves
+ *                      (both -1 or both >= 0); children after their parent is
+ *                      not required, but every tree must be a proper binary tree
+ *   feature            host, split feature in [0, n_features) (ignored at leaves)
+ *   threshold          host, fp32 split value
+ *   default_left       host, 1 if NaN goes left (may be NULL: NaN goes left)
+ *   z                  host, edge weight into the node, 0 < z <= 1 (root ignored)
+ *   leaf_value         host, value at leaves (ignored at internal nodes)
+ *   n_features         number of features F, 1..QTS_MAX_FEATURES
+ *   flags              0 or QTS_FLAG_FP64
+ *   out                receives the handle; free with qts_free
+ * Errors: QTS_ERR_ARG (bad pointers/topology/z), QTS_ERR_UNSUPPORTED (a path
+ * with more than QTS_MAX_UNIQUE_FEATURES_PER_PATH unique features), QTS_ERR_OOM,
+ * QTS_ERR_CUDA.  Synchronous (uploads with cudaMemcpy on the current device).
+ */
+qts_status qts_load_ensemble(int32_t n_trees, const int64_t *tree_node_offsets,
+                             const int32_t *left, const int32_t *right, const int32_t *feature,
+                             const float *threshold, const uint8_t *default_left, const float *z,
+                             const float *leaf_value, int32_t n_features, uint32_t flags,
+                             qts_ensemble **out);
+
+/*
+ * qts_update_params - replace edge weights and leaf values (same topology) and
+ * rebuild the path tables (Sec. 2).  z, leaf_value: host, one entry per node.
+ * Synchronous.  Errors as qts_load_ensemble.
+ */
+qts_status qts_update_params(qts_ensemble *ens, const float *z, const float *leaf_value);
+
+/*
+ * qts_shap_values - first-order Shapley values (Thm 1 with S = {i}, Eq.
+ * shap_as_weighted_banzhafs, Alg. 1 with s = 1).
+ *   X       device, M x F fp32 row-major
+ *   M       samples (>= 0; 0 is a no-op), F must equal the ensemble's n_features
+ *   n_quad  Gauss-Legendre points, 1..QTS_MAX_QUAD (8 is the fast path)
+ *   phi     device, M x (F+1) fp64, overwritten; phi[s][F] = E[f] = sum_v R_empty^v
+ *           (the bias, so that sum_f phi[s][f] = f(x_s))
+ * Per-path arithmetic is FP32 (FP64 with QTS_FLAG_FP64); contributions are
+ * accumulated in FP32 over at most a few thousand paths, then in FP64 across
+ * path chunks and trees.
+ */
+qts_status qts_shap_values(qts_ensemble *ens, const float *X, int64_t M, int32_t F,
+                           int32_t n_quad, double *phi, qts_stream_t stream);
+
+/*
+ * qts_shap_interactions - pairwise Shapley interaction values (Thm 1 with
+ * S = {i,j}; Alg. 1 with s = 2) in the pred_interactions layout:
+ *   phi_ij  device, M x (F+1) x (F+1) fp32, overwritten:
+ *           [s][i][j] = SII_ij / 2 for i != j < F,
+ *           [s][i][i] = phi_i - sum_{j != i} SII_ij / 2 (rows sum to phi_i),
+ *           [s][F][F] = E[f], other entries of row/column F are 0.
+ * Cross-tree accumulation is FP64 in the ensemble's workspace (device memory
+ * of M * (F(F+1)/2) doubles, grown on demand with cudaMalloc).
+ */
+qts_status qts_shap_interactions(qts_ensemble *ens, const float *X, int64_t M, int32_t F,
+                                 int32_t n_quad, float *phi_ij, qts_stream_t stream);
+
+/*
+ * qts_shap_backward - adjoint of qts_shap_values.  With
+ * L = sum_s sum_{f <= F} grad_phi[s][f] * phi[s][f]:
+ *   d_leaf  device, N fp64 (N = total nodes), overwritten: dL/d leaf_value[n]
+ *           (0 at internal nodes)
+ *   d_z     device, N fp64, overwritten: dL/d z[n] (0 at roots)
+ * The paper has no adjoint; this differentiates Thm 1 / Eq.
+ * shap_as_weighted_banzhafs with the same n_quad rule, recomputing per-path
+ * products instead of storing them.
+ *   grad_phi device, M x (F+1) fp32 (column F weights the bias E[f]).
+ */
+qts_status qts_shap_backward(qts_ensemble *ens, const float *X, int64_t M, int32_t F,
+                             int32_t n_quad, const float *grad_phi, double *d_leaf, double *d_z,
+                             qts_stream_t stream);
+
+/* One request of a batched call; all pointers are device pointers. */
+typedef struct qts_request {
+    qts_ensemble *ens;
+    const float *X;        /* M x F */
+    int64_t M;
+    int32_t F;
+    const float *grad_phi; /* M x (F+1); NULL = forward only */
+    double *phi;           /* M x (F+1), overwritten (may be NULL when grad_phi != NULL) */
+    double *d_leaf;        /* N, overwritten (ignored when grad_phi == NULL) */
+    double *d_z;           /* N, overwritten (ignored when grad_phi == NULL) */
+} qts_request;
+
+/*
+ * qts_batched_fwd_bwd - forward (and, where grad_phi is given, backward) of many
+ * heterogeneous requests in ONE persistent kernel launch: a device work list of
+ * (request, path bucket, path chunk, sample tile) items sorted by cost is
+ * consumed through an atomic counter, and one pass over each (sample, path)
+ * produces both phi and the adjoint (the forward product terms are a subset of
+ * the adjoint's).  The whole call (initialisation, persistent kernel, adjoint
+ * epilogue) is captured once into a CUDA graph keyed by the request set and
+ * replayed on later calls with the same requests.  Each ensemble may appear in
+ * at most one request of a call.  FP32 ensembles only.
+ */
+qts_status qts_batched_fwd_bwd(int32_t n_requests, const qts_request *reqs, int32_t n_quad,
+                               qts_stream_t stream);
+
+/*
+ * qts_autotune - time candidate launch configurations (warps per block, paths
+ * per chunk, node-group width) for this ensemble and sample count on `stream`,
+ * keep the fastest in the ensemble, and, if cache_path is not NULL, merge the
+ * result into that JSON file keyed by (bucket width, F range, M range).
+ * X: device M x F.  Synchronous.  Scratch output is allocated internally.
+ */
+qts_status qts_autotune(qts_ensemble *ens, const float *X, int64_t M, int32_t F,
+                        const char *cache_path, qts_stream_t stream);
+
+/* Read and clear the ensemble's device status word after synchronising `stream`. */
+qts_status qts_sync_status(qts_ensemble *ens, qts_stream_t stream);
+
+/* Summary of the prepared path tables. */
+typedef struct qts_info {
+    int32_t n_trees, n_features;
+    int64_t n_nodes, n_leaves, n_paths;   /* paths with >= 1 unique feature */
+    int32_t max_unique;                   /* d = max unique features on a path */
+    int64_t sum_unique;                   /* sum over paths of unique features */
+    int32_t n_buckets;
+    int32_t bucket_width[32];
+    int64_t bucket_paths[32];
+    double expected_value;                /* E[f] */
+    int64_t device_bytes;                 /* path tables + adjoint metadata */
+    uint32_t flags;
+} qts_info;
+qts_status qts_get_info(const qts_ensemble *ens, qts_info *out);
+
+/*
+ * qts_describe_ensemble - host-only dry run of qts_load_ensemble's path
+ * preparation (Sec. 2 merging and bucketing): same arguments and checks, no
+ * device memory is touched; fills `out` (device_bytes = the bytes an upload
+ * would take).  Usable without a GPU.
+ */
+qts_status qts_describe_ensemble(int32_t n_trees, const int64_t *tree_node_offsets,
+                                 const int32_t *left, const int32_t *right, const int32_t *feature,
+                                 const float *threshold, const uint8_t *default_left,
+                                 const float *z, const float *leaf_value, int32_t n_features,
+                                 uint32_t flags, qts_info *out);
+
+/* Gauss-Legendre nodes/weights on [0,1] used by the kernels (fp64, ascending). */
+qts_status qts_gauss_legendre(int32_t n, double *t, double *w);
+
+/* Thread-local description of the last error (never NULL). */
+const char *qts_last_error(void);
+
+/* Free the handle and its device memory (synchronises the device first). NULL is a no-op. */
+void qts_free(qts_ensemble *ens);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,302 @@
+"""Python binding of libqtreeshap (GB300 Quadrature-TreeSHAP).
+
+Thin ctypes marshalling over the C ABI declared in ``include/qtreeshap.h``;
+every step of the computation runs in the library's CUDA kernels.  PyTorch is
+used only for device memory and streams.  If the shared library has not been
+built (``__graft_entry__.build()`` or ``python paper_2605_04497_gb300/build.py``)
+importing the compute functions raises - there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqtreeshap.so")
+
+QTS_OK = 0
+QTS_FLAG_FP64 = 1
+STATUS_NAMES = {0: "QTS_OK", 1: "QTS_ERR_ARG", 2: "QTS_ERR_CUDA", 3: "QTS_ERR_OOM",
+                4: "QTS_ERR_UNSUPPORTED", 5: "QTS_ERR_TIMEOUT", 6: "QTS_ERR_DEVICE_CHECK"}
+
+# every symbol include/qtreeshap.h declares
+EXPORTS = ("qts_load_ensemble", "qts_update_params", "qts_shap_values", "qts_shap_interactions",
+           "qts_shap_backward", "qts_batched_fwd_bwd", "qts_autotune", "qts_sync_status",
+           "qts_get_info", "qts_describe_ensemble", "qts_gauss_legendre", "qts_last_error",
+           "qts_free")
+
+_lib = None
+
+
+class QtsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class QtsInfo(ctypes.Structure):
+    _fields_ = [
+        ("n_trees", ctypes.c_int32), ("n_features", ctypes.c_int32),
+        ("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64), ("n_paths", ctypes.c_int64),
+        ("max_unique", ctypes.c_int32), ("sum_unique", ctypes.c_int64),
+        ("n_buckets", ctypes.c_int32), ("bucket_width", ctypes.c_int32 * 32),
+        ("bucket_paths", ctypes.c_int64 * 32), ("expected_value", ctypes.c_double),
+        ("device_bytes", ctypes.c_int64), ("flags", ctypes.c_uint32),
+    ]
+
+
+class QtsRequest(ctypes.Structure):
+    _fields_ = [
+        ("ens", ctypes.c_void_p), ("X", ctypes.c_void_p), ("M", ctypes.c_int64),
+        ("F", ctypes.c_int32), ("grad_phi", ctypes.c_void_p), ("phi", ctypes.c_void_p),
+        ("d_leaf", ctypes.c_void_p), ("d_z", ctypes.c_void_p),
+    ]
+
+
+def lib():
+    """Load the shared library (raises if it is missing: no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+        L.qts_load_ensemble.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, u32,
+                                        ctypes.POINTER(vp)]
+        L.qts_update_params.argtypes = [vp, vp, vp]
+        L.qts_shap_values.argtypes = [vp, vp, i64, i32, i32, vp, vp]
+        L.qts_shap_interactions.argtypes = [vp, vp, i64, i32, i32, vp, vp]
+        L.qts_shap_backward.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, vp]
+        L.qts_batched_fwd_bwd.argtypes = [i32, vp, i32, vp]
+        L.qts_autotune.argtypes = [vp, vp, i64, i32, ctypes.c_char_p, vp]
+        L.qts_sync_status.argtypes = [vp, vp]
+        L.qts_get_info.argtypes = [vp, ctypes.POINTER(QtsInfo)]
+        L.qts_describe_ensemble.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, u32,
+                                            ctypes.POINTER(QtsInfo)]
+        L.qts_gauss_legendre.argtypes = [i32, vp, vp]
+        L.qts_last_error.argtypes = []
+        L.qts_last_error.restype = ctypes.c_char_p
+        L.qts_free.argtypes = [vp]
+        L.qts_free.restype = None
+        for f in EXPORTS:
+            if f not in ("qts_last_error", "qts_free"):
+                getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != QTS_OK:
+        raise QtsError(status, lib().qts_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def gauss_legendre(n: int):
+    t = np.zeros(n)
+    w = np.zeros(n)
+    _check(lib().qts_gauss_legendre(n, t.ctypes.data, w.ctypes.data))
+    return t, w
+
+
+def _info_dict(i: QtsInfo) -> dict:
+    nb = i.n_buckets
+    return dict(n_trees=i.n_trees, n_features=i.n_features, n_nodes=i.n_nodes,
+                n_leaves=i.n_leaves, n_paths=i.n_paths, max_unique=i.max_unique,
+                sum_unique=i.sum_unique, buckets=list(zip(i.bucket_width[:nb], i.bucket_paths[:nb])),
+                expected_value=i.expected_value, device_bytes=i.device_bytes, flags=i.flags)
+
+
+def describe(ens, fp64: bool = False) -> dict:
+    """Host-only path preparation summary (no GPU needed)."""
+    arr = lambda a, dt: np.ascontiguousarray(a, dtype=dt)
+    a = [arr(ens.node_offsets, np.int64), arr(ens.left, np.int32), arr(ens.right, np.int32),
+         arr(ens.feature, np.int32), arr(ens.threshold, np.float32), arr(ens.default_left, np.uint8),
+         arr(ens.z, np.float32), arr(ens.leaf_value, np.float32)]
+    i = QtsInfo()
+    _check(lib().qts_describe_ensemble(len(a[0]) - 1, *[x.ctypes.data for x in a], int(ens.n_features),
+                                       QTS_FLAG_FP64 if fp64 else 0, ctypes.byref(i)))
+    return _info_dict(i)
+
+
+class Ensemble:
+    """A tree ensemble loaded into device path tables (owns the C handle)."""
+
+    def __init__(self, node_offsets, left, right, feature, threshold, default_left, z, leaf_value,
+                 n_features: int, fp64: bool = False):
+        arr = lambda a, dt: np.ascontiguousarray(a, dtype=dt)
+        self._off = arr(node_offsets, np.int64)
+        self._host = dict(left=arr(left, np.int32), right=arr(right, np.int32),
+                          feature=arr(feature, np.int32), threshold=arr(threshold, np.float32),
+                          default_left=arr(default_left, np.uint8), z=arr(z, np.float32),
+                          leaf_value=arr(leaf_value, np.float32))
+        self.n_features = int(n_features)
+        self.n_trees = len(self._off) - 1
+        self.n_nodes = int(self._off[-1])
+        self.fp64 = bool(fp64)
+        h = ctypes.c_void_p()
+        H = self._host
+        _check(lib().qts_load_ensemble(self.n_trees, self._off.ctypes.data, H["left"].ctypes.data,
+                                       H["right"].ctypes.data, H["feature"].ctypes.data,
+                                       H["threshold"].ctypes.data, H["default_left"].ctypes.data,
+                                       H["z"].ctypes.data, H["leaf_value"].ctypes.data,
+                                       self.n_features, QTS_FLAG_FP64 if fp64 else 0,
+                                       ctypes.byref(h)))
+        self.handle = h
+
+    @classmethod
+    def from_arrays(cls, ens, fp64: bool = False) -> "Ensemble":
+        """From any object with node_offsets/left/right/feature/threshold/
+        default_left/z/leaf_value/n_features attributes."""
+        return cls(ens.node_offsets, ens.left, ens.right, ens.feature, ens.threshold,
+                   ens.default_left, ens.z, ens.leaf_value, ens.n_features, fp64=fp64)
+
+    def update_params(self, z, leaf_value):
+        z = np.ascontiguousarray(z, dtype=np.float32)
+        lv = np.ascontiguousarray(leaf_value, dtype=np.float32)
+        assert z.shape == (self.n_nodes,) and lv.shape == (self.n_nodes,)
+        _check(lib().qts_update_params(self.handle, z.ctypes.data, lv.ctypes.data))
+        self._host["z"], self._host["leaf_value"] = z, lv
+
+    def info(self) -> dict:
+        i = QtsInfo()
+        _check(lib().qts_get_info(self.handle, ctypes.byref(i)))
+        return _info_dict(i)
+
+    def sync_status(self, stream=None):
+        _check(lib().qts_sync_status(self.handle, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().qts_free(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _check_x(ens: Ensemble, X):
+    import torch
+
+    assert isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32, "X: cuda float32"
+    assert X.dim() == 2 and X.shape[1] == ens.n_features and X.is_contiguous(), "X: M x F contiguous"
+
+
+def shap_values(ens: Ensemble, X, n_quad: int = 8, out=None, stream=None):
+    """phi (M x (F+1), float64, last column E[f]) on X's device."""
+    import torch
+
+    _check_x(ens, X)
+    M, F = X.shape
+    if out is None:
+        out = torch.empty((M, F + 1), dtype=torch.float64, device=X.device)
+    _check(lib().qts_shap_values(ens.handle, _ptr(X), M, F, n_quad, _ptr(out), _stream(stream)))
+    return out
+
+
+def shap_interactions(ens: Ensemble, X, n_quad: int = 8, out=None, stream=None):
+    """M x (F+1) x (F+1) float32: off-diagonal SII/2, diagonal phi_i - row sum, E[f] at [F,F]."""
+    import torch
+
+    _check_x(ens, X)
+    M, F = X.shape
+    if out is None:
+        out = torch.empty((M, F + 1, F + 1), dtype=torch.float32, device=X.device)
+    _check(lib().qts_shap_interactions(ens.handle, _ptr(X), M, F, n_quad, _ptr(out),
+                                       _stream(stream)))
+    return out
+
+
+def shap_backward(ens: Ensemble, X, grad_phi, n_quad: int = 8, stream=None):
+    """(d_leaf, d_z), float64 of length n_nodes: gradients of sum(grad_phi * phi)."""
+    import torch
+
+    _check_x(ens, X)
+    M, F = X.shape
+    assert grad_phi.shape == (M, F + 1) and grad_phi.dtype == torch.float32 and grad_phi.is_contiguous()
+    d_leaf = torch.empty(ens.n_nodes, dtype=torch.float64, device=X.device)
+    d_z = torch.empty(ens.n_nodes, dtype=torch.float64, device=X.device)
+    _check(lib().qts_shap_backward(ens.handle, _ptr(X), M, F, n_quad, _ptr(grad_phi), _ptr(d_leaf),
+                                   _ptr(d_z), _stream(stream)))
+    return d_leaf, d_z
+
+
+def make_requests(items):
+    """items: list of dicts with ens, X, grad_phi (optional), phi, d_leaf, d_z tensors."""
+    reqs = (QtsRequest * len(items))()
+    for r, it in zip(reqs, items):
+        X = it["X"]
+        r.ens = it["ens"].handle.value
+        r.X = X.data_ptr()
+        r.M = X.shape[0]
+        r.F = X.shape[1]
+        r.grad_phi = it["grad_phi"].data_ptr() if it.get("grad_phi") is not None else 0
+        r.phi = it["phi"].data_ptr() if it.get("phi") is not None else 0
+        r.d_leaf = it["d_leaf"].data_ptr() if it.get("d_leaf") is not None else 0
+        r.d_z = it["d_z"].data_ptr() if it.get("d_z") is not None else 0
+    return reqs
+
+
+def batched_fwd_bwd(reqs, n_quad: int = 8, stream=None):
+    """Run prepared ``make_requests`` in one persistent launch (graph-captured)."""
+    _check(lib().qts_batched_fwd_bwd(len(reqs), ctypes.cast(reqs, ctypes.c_void_p), n_quad,
+                                     _stream(stream)))
+
+
+def autotune(ens: Ensemble, X, cache_path: str | None = None, stream=None):
+    _check_x(ens, X)
+    M, F = X.shape
+    _check(lib().qts_autotune(ens.handle, _ptr(X), M, F,
+                              cache_path.encode() if cache_path else None, _stream(stream)))
+
+
+class QTreeShapFn:
+    """torch.autograd.Function: phi = QTreeShap(leaf_values, z; X).
+
+    ``leaf_values`` and ``z`` are float32 tensors of length n_nodes (the
+    ensemble's parameters); backward returns dL/d leaf_values and dL/d z from the
+    adjoint kernel (float64 results cast to the parameters' dtype)."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, ens: Ensemble, leaf_values, z, X, n_quad: int = 8):
+        if cls._fn is None:
+            import torch
+
+            class _F(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, leaf_values, z, X, ens, n_quad):
+                    lv = leaf_values.detach().cpu().numpy()
+                    zz = z.detach().cpu().numpy()
+                    if not (np.array_equal(lv, ens._host["leaf_value"]) and
+                            np.array_equal(zz, ens._host["z"])):
+                        ens.update_params(zz, lv)
+                    ctx.ens, ctx.n_quad = ens, n_quad
+                    ctx.save_for_backward(X)
+                    return shap_values(ens, X, n_quad)
+
+                @staticmethod
+                def backward(ctx, grad_phi):
+                    (X,) = ctx.saved_tensors
+                    g = grad_phi.to(torch.float32).contiguous()
+                    d_leaf, d_z = shap_backward(ctx.ens, X, g, ctx.n_quad)
+                    return d_leaf.to(torch.float32), d_z.to(torch.float32), None, None, None
+
+            cls._fn = _F
+        return cls._fn.apply(leaf_values, z, X, ens, n_quad)

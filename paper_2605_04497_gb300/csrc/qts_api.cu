@@ -1,0 +1,321 @@
+// C-ABI entry points: handle lifecycle, argument checks, per-bucket launches.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "qts_internal.h"
+
+namespace qts {
+
+static thread_local std::string g_err = "no error";
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+qts_status fail(qts_status st, const std::string& msg) {
+    g_err = msg;
+    return st;
+}
+
+qts_status cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? QTS_ERR_OOM : QTS_ERR_CUDA;
+}
+
+int num_sms() {
+    static int sms = 0;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 152;
+    });
+    return sms;
+}
+
+static Tune default_tune(int D) {
+    Tune t;
+    t.warps = 4;
+    t.sub = D <= 16 ? 32 : 16;
+    t.paths = D <= 8 ? 512 : (D <= 16 ? 256 : 128);
+    t.np = D <= 8 ? 8 : (D <= 24 ? 4 : 2);
+    return t;
+}
+
+void release_device(qts_ensemble* e) {
+    cudaFree(e->d_rec);
+    cudaFree(e->d_path_leaf);
+    cudaFree(e->d_path_zprod);
+    cudaFree(e->d_slot_edge_begin);
+    cudaFree(e->d_edge_node);
+    cudaFree(e->d_edge_coef);
+    cudaFree(e->d_empty_leaf);
+    e->d_rec = nullptr;
+    e->d_path_leaf = nullptr;
+    e->d_path_zprod = nullptr;
+    e->d_slot_edge_begin = nullptr;
+    e->d_edge_node = nullptr;
+    e->d_edge_coef = nullptr;
+    e->d_empty_leaf = nullptr;
+    e->device_bytes = 0;
+}
+
+template <typename T>
+static qts_status up(T** dst, const std::vector<T>& src, int64_t* total, const char* what) {
+    size_t bytes = std::max<size_t>(src.size(), 1) * sizeof(T);
+    cudaError_t err = cudaMalloc((void**)dst, bytes);
+    if (err != cudaSuccess) return cuda_fail(err, what);
+    if (!src.empty()) {
+        err = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+        if (err != cudaSuccess) return cuda_fail(err, what);
+    }
+    *total += (int64_t)bytes;
+    return QTS_OK;
+}
+
+qts_status upload(qts_ensemble* e) {
+    const Prepared& P = e->prep;
+    int64_t tot = 0;
+    qts_status st = QTS_OK;
+    if (e->flags & QTS_FLAG_FP64) st = up((Rec64**)&e->d_rec, P.rec64, &tot, "upload path tables");
+    else st = up((Rec32**)&e->d_rec, P.rec32, &tot, "upload path tables");
+    if (st == QTS_OK) st = up(&e->d_path_leaf, P.path_leaf, &tot, "upload path leaves");
+    if (st == QTS_OK) st = up(&e->d_path_zprod, P.path_zprod, &tot, "upload path products");
+    if (st == QTS_OK) st = up(&e->d_slot_edge_begin, P.slot_edge_begin, &tot, "upload element edges");
+    if (st == QTS_OK) st = up(&e->d_edge_node, P.edge_node, &tot, "upload edge nodes");
+    if (st == QTS_OK) st = up(&e->d_edge_coef, P.edge_coef, &tot, "upload edge coefficients");
+    if (st == QTS_OK) st = up(&e->d_empty_leaf, P.empty_leaf, &tot, "upload single-leaf trees");
+    if (st != QTS_OK) {
+        release_device(e);
+        return st;
+    }
+    e->device_bytes = tot;
+    return QTS_OK;
+}
+
+qts_status ensure_workspace(qts_ensemble* e, size_t bytes) {
+    if (bytes <= e->work_bytes) return QTS_OK;
+    if (e->d_work) {
+        cudaError_t err = cudaDeviceSynchronize();
+        if (err != cudaSuccess) return cuda_fail(err, "workspace resize sync");
+        cudaFree(e->d_work);
+        e->d_work = nullptr;
+        e->work_bytes = 0;
+    }
+    size_t want = std::max(bytes, (size_t)1 << 20);
+    cudaError_t err = cudaMalloc(&e->d_work, want);
+    if (err != cudaSuccess) return cuda_fail(err, "workspace allocation");
+    e->work_bytes = want;
+    return QTS_OK;
+}
+
+qts_status check_call(qts_ensemble* e, const float* X, int64_t M, int32_t F, int32_t n_quad) {
+    if (!e) return fail(QTS_ERR_ARG, "ensemble handle is NULL");
+    if (F != e->n_features)
+        return fail(QTS_ERR_ARG, "F = " + std::to_string(F) + " does not match the ensemble's " +
+                                     std::to_string(e->n_features) + " features");
+    if (M < 0) return fail(QTS_ERR_ARG, "M must be >= 0");
+    if (M > 0 && !X) return fail(QTS_ERR_ARG, "X is NULL");
+    if (M > ((int64_t)1 << 31)) return fail(QTS_ERR_UNSUPPORTED, "M above 2^31 samples");
+    if (n_quad < 1 || n_quad > QTS_MAX_QUAD)
+        return fail(QTS_ERR_ARG, "n_quad must be in [1, " + std::to_string(QTS_MAX_QUAD) + "]");
+    return QTS_OK;
+}
+
+}  // namespace qts
+
+using namespace qts;
+
+extern "C" {
+
+const char* qts_last_error(void) { return g_err.c_str(); }
+
+qts_status qts_gauss_legendre(int32_t n, double* t, double* w) {
+    if (!t || !w || n < 1 || n > 64) return fail(QTS_ERR_ARG, "n must be in [1, 64] and t, w non-NULL");
+    return gauss_legendre(n, t, w) ? QTS_OK : fail(QTS_ERR_ARG, "gauss_legendre failed");
+}
+
+qts_status qts_load_ensemble(int32_t n_trees, const int64_t* off, const int32_t* left,
+                             const int32_t* right, const int32_t* feature, const float* threshold,
+                             const uint8_t* default_left, const float* z, const float* leaf_value,
+                             int32_t n_features, uint32_t flags, qts_ensemble** out) {
+    if (!out) return fail(QTS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_trees < 1 || !off || !left || !right || !feature || !threshold || !z || !leaf_value)
+        return fail(QTS_ERR_ARG, "n_trees < 1 or a required array is NULL");
+    if (n_features < 1 || n_features > QTS_MAX_FEATURES)
+        return fail(QTS_ERR_UNSUPPORTED, "n_features must be in [1, " + std::to_string(QTS_MAX_FEATURES) + "]");
+    if (flags & ~QTS_FLAG_FP64) return fail(QTS_ERR_ARG, "unknown flags");
+    for (int t = 0; t < n_trees; ++t)
+        if (off[t + 1] <= off[t]) return fail(QTS_ERR_ARG, "tree_node_offsets must be increasing");
+    if (off[0] != 0) return fail(QTS_ERR_ARG, "tree_node_offsets[0] must be 0");
+    auto* e = new (std::nothrow) qts_ensemble();
+    if (!e) return fail(QTS_ERR_OOM, "host allocation");
+    const int64_t N = off[n_trees];
+    e->n_trees = n_trees;
+    e->n_features = n_features;
+    e->n_nodes = N;
+    e->flags = flags;
+    cudaGetDevice(&e->device);
+    e->off.assign(off, off + n_trees + 1);
+    e->left.assign(left, left + N);
+    e->right.assign(right, right + N);
+    e->feature.assign(feature, feature + N);
+    e->thr.assign(threshold, threshold + N);
+    e->z.assign(z, z + N);
+    e->leaf.assign(leaf_value, leaf_value + N);
+    if (default_left) e->defl.assign(default_left, default_left + N);
+    else e->defl.assign((size_t)N, 1);
+    std::string err;
+    qts_status st = prepare(n_trees, e->off.data(), e->left.data(), e->right.data(),
+                            e->feature.data(), e->thr.data(), e->defl.data(), e->z.data(),
+                            e->leaf.data(), n_features, (flags & QTS_FLAG_FP64) != 0, &e->prep, &err);
+    if (st != QTS_OK) {
+        delete e;
+        return fail(st, err);
+    }
+    cudaError_t ce = cudaMalloc(&e->d_status, sizeof(int));
+    if (ce == cudaSuccess) ce = cudaMemset(e->d_status, 0, sizeof(int));
+    if (ce != cudaSuccess) {
+        delete e;
+        return cuda_fail(ce, "status word");
+    }
+    st = upload(e);
+    if (st != QTS_OK) {
+        cudaFree(e->d_status);
+        delete e;
+        return st;
+    }
+    for (int D = 0; D <= kMaxD; ++D) e->tune[D] = default_tune(std::max(D, 1));
+    *out = e;
+    return QTS_OK;
+}
+
+qts_status qts_update_params(qts_ensemble* e, const float* z, const float* leaf_value) {
+    if (!e || !z || !leaf_value) return fail(QTS_ERR_ARG, "NULL argument");
+    std::vector<float> z0 = e->z, l0 = e->leaf;
+    e->z.assign(z, z + e->n_nodes);
+    e->leaf.assign(leaf_value, leaf_value + e->n_nodes);
+    Prepared P;
+    std::string err;
+    qts_status st = prepare(e->n_trees, e->off.data(), e->left.data(), e->right.data(),
+                            e->feature.data(), e->thr.data(), e->defl.data(), e->z.data(),
+                            e->leaf.data(), e->n_features, (e->flags & QTS_FLAG_FP64) != 0, &P, &err);
+    if (st != QTS_OK) {
+        e->z = z0;
+        e->leaf = l0;
+        return fail(st, err);
+    }
+    cudaError_t ce = cudaDeviceSynchronize();
+    if (ce != cudaSuccess) return cuda_fail(ce, "update sync");
+    release_device(e);
+    e->prep = std::move(P);
+    return upload(e);
+}
+
+qts_status qts_shap_values(qts_ensemble* e, const float* X, int64_t M, int32_t F, int32_t n_quad,
+                           double* phi, qts_stream_t stream) {
+    qts_status st = check_call(e, X, M, F, n_quad);
+    if (st != QTS_OK) return st;
+    if (M == 0) return QTS_OK;
+    if (!phi) return fail(QTS_ERR_ARG, "phi is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    QuadF qf;
+    QuadD qd;
+    if (!make_quad(n_quad, &qf, &qd)) return fail(QTS_ERR_ARG, "quadrature rule");
+    cudaError_t ce = launch_phi_init(phi, M, F, e->prep.bias, s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "phi init launch");
+    for (const Bucket& b : e->prep.buckets) {
+        ce = launch_fwd_bucket(e, b, X, M, F, qf, qd, phi, e->tune[b.D], s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "forward kernel launch");
+    }
+    return QTS_OK;
+}
+
+qts_status qts_sync_status(qts_ensemble* e, qts_stream_t stream) {
+    if (!e) return fail(QTS_ERR_ARG, "ensemble handle is NULL");
+    cudaError_t ce = cudaStreamSynchronize((cudaStream_t)stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "stream synchronize");
+    int h = 0;
+    ce = cudaMemcpy(&h, e->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return cuda_fail(ce, "status read");
+    if (h != 0) {
+        cudaMemset(e->d_status, 0, sizeof(int));
+        return fail((qts_status)h, h == QTS_ERR_TIMEOUT ? "a bounded device wait ran out"
+                                                        : "device-side check failed");
+    }
+    return QTS_OK;
+}
+
+qts_status qts_get_info(const qts_ensemble* e, qts_info* out) {
+    if (!e || !out) return fail(QTS_ERR_ARG, "NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    out->n_trees = e->n_trees;
+    out->n_features = e->n_features;
+    out->n_nodes = e->n_nodes;
+    out->n_leaves = e->prep.n_leaves;
+    out->n_paths = e->prep.n_paths;
+    out->max_unique = e->prep.max_unique;
+    out->sum_unique = e->prep.sum_unique;
+    out->n_buckets = (int32_t)e->prep.buckets.size();
+    for (size_t i = 0; i < e->prep.buckets.size() && i < 32; ++i) {
+        out->bucket_width[i] = e->prep.buckets[i].D;
+        out->bucket_paths[i] = e->prep.buckets[i].n_paths;
+    }
+    out->expected_value = e->prep.bias;
+    out->device_bytes = e->device_bytes;
+    out->flags = e->flags;
+    return QTS_OK;
+}
+
+qts_status qts_describe_ensemble(int32_t n_trees, const int64_t* off, const int32_t* left,
+                                 const int32_t* right, const int32_t* feature, const float* threshold,
+                                 const uint8_t* default_left, const float* z, const float* leaf_value,
+                                 int32_t n_features, uint32_t flags, qts_info* out) {
+    if (!out || n_trees < 1 || !off || !left || !right || !feature || !threshold || !z || !leaf_value)
+        return fail(QTS_ERR_ARG, "NULL argument or n_trees < 1");
+    if (n_features < 1 || n_features > QTS_MAX_FEATURES)
+        return fail(QTS_ERR_UNSUPPORTED, "n_features out of range");
+    for (int t = 0; t < n_trees; ++t)
+        if (off[t + 1] <= off[t]) return fail(QTS_ERR_ARG, "tree_node_offsets must be increasing");
+    std::vector<uint8_t> defl;
+    if (!default_left) defl.assign((size_t)off[n_trees], 1);
+    Prepared P;
+    std::string err;
+    const bool fp64 = (flags & QTS_FLAG_FP64) != 0;
+    qts_status st = prepare(n_trees, off, left, right, feature, threshold,
+                            default_left ? default_left : defl.data(), z, leaf_value, n_features,
+                            fp64, &P, &err);
+    if (st != QTS_OK) return fail(st, err);
+    std::memset(out, 0, sizeof(*out));
+    out->n_trees = n_trees;
+    out->n_features = n_features;
+    out->n_nodes = off[n_trees];
+    out->n_leaves = P.n_leaves;
+    out->n_paths = P.n_paths;
+    out->max_unique = P.max_unique;
+    out->sum_unique = P.sum_unique;
+    out->n_buckets = (int32_t)P.buckets.size();
+    for (size_t i = 0; i < P.buckets.size() && i < 32; ++i) {
+        out->bucket_width[i] = P.buckets[i].D;
+        out->bucket_paths[i] = P.buckets[i].n_paths;
+    }
+    out->expected_value = P.bias;
+    out->device_bytes = (int64_t)((fp64 ? P.rec64.size() * sizeof(Rec64) : P.rec32.size() * sizeof(Rec32)) +
+                                  P.path_leaf.size() * 8 + P.path_zprod.size() * 8 +
+                                  P.slot_edge_begin.size() * 8 + P.edge_node.size() * 16);
+    out->flags = flags;
+    return QTS_OK;
+}
+
+void qts_free(qts_ensemble* e) {
+    if (!e) return;
+    cudaDeviceSynchronize();
+    release_device(e);
+    cudaFree(e->d_status);
+    cudaFree(e->d_work);
+    delete e;
+}
+
+}  // extern "C"

@@ -1,0 +1,340 @@
+// First-order Shapley values (Thm 1 with S = {i}, Eq. shap_as_weighted_banzhafs).
+//
+// Work decomposition: a block owns a tile of 32 samples (lane = sample) and a
+// chunk of paths of one bucket (all paths have D merged elements).  Its warps
+// take the chunk's paths round-robin; every lane evaluates, for its sample,
+//     c_i = sum_m w_m val prod_{j<i} a_j(t_m) prod_{j>i} a_j(t_m),
+//     a_j(t) = z_j + t (o_j - z_j),
+// by a prefix product (seeded with w_m * val) and a suffix product - no
+// division - with two quadrature nodes packed per f32x2 register pair, and
+// adds (o_i - z_i) c_i to phi[s, f_i] in a shared FP32 tile.  Path records are
+// staged in shared memory by bulk (TMA) copies, double-buffered; the FP32 tile
+// is flushed into the FP64 output with atomics once per block.
+#include <algorithm>
+#include <type_traits>
+
+#include "qts_device.cuh"
+
+namespace qts {
+
+struct FwdArgs {
+    const void* rec;    // bucket records (Rec32 or Rec64)
+    int64_t n_paths;
+    int64_t paths_per_block;
+    int sub;            // paths per staged sub-chunk
+    int n_tiles;        // sample tiles of 32
+    const float* X;
+    int64_t M;
+    int F;
+    double* phi;        // M x (F+1)
+    int* status;
+    QuadF q;
+    QuadD qd;
+};
+
+// ------------------------------------------------------------------ FP32 --
+
+template <int D, int NP, bool HAS_NAN>
+__device__ __forceinline__ void fwd_path_f32(const Rec32* __restrict__ r, const float* __restrict__ xs,
+                                             float* ps, int lane, const QuadF& q) {
+    constexpr int K = NP / 2;  // node pairs per pass
+    const float val = r[0].z;
+    float dd[D], zz[D];
+    int ff[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const Rec32 e = r[1 + j];
+        const int f = feat_of(e.bits);
+        const float x = xs[f * kTileLd + lane];
+        const bool o = satisfies<HAS_NAN>(x, e.lo, e.hi, e.bits);
+        dd[j] = (o ? 1.f : 0.f) - e.z;
+        zz[j] = e.z;
+        ff[j] = f;
+    }
+    float cacc[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) cacc[j] = 0.f;
+    const int npass = q.n_pad / NP;
+    for (int pass = 0; pass < npass; ++pass) {
+        float2 T[K], P[D][K], A[D][K], S[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int m = pass * NP + 2 * k;
+            T[k] = f2(q.t[m], q.t[m + 1]);
+            P[0][k] = f2(q.w[m] * val, q.w[m + 1] * val);
+        }
+        // prefix products P_j = w val prod_{l<j} a_l
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                A[j][k] = fma2(T[k], f2s(dd[j]), f2s(zz[j]));
+                if (j + 1 < D) P[j + 1][k] = mul2(P[j][k], A[j][k]);
+            }
+        }
+        // suffix products, combined on the way down
+#pragma unroll
+        for (int k = 0; k < K; ++k) S[k] = f2s(1.f);
+#pragma unroll
+        for (int j = D - 1; j >= 0; --j) {
+            float2 acc = mul2(P[j][0], S[0]);
+#pragma unroll
+            for (int k = 1; k < K; ++k) acc = fma2(P[j][k], S[k], acc);
+            if (j > 0) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) S[k] = mul2(S[k], A[j][k]);
+            }
+            cacc[j] += acc.x + acc.y;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) atomicAdd(&ps[ff[j] * kTileLd + lane], dd[j] * cacc[j]);
+}
+
+// ------------------------------------------------------------------ FP64 --
+
+template <int D, bool HAS_NAN>
+__device__ __forceinline__ void fwd_path_f64(const Rec64* __restrict__ r, const float* __restrict__ xs,
+                                             double* ps, int lane, const QuadD& q) {
+    const double val = r[0].z;
+    double dd[D], zz[D], cacc[D];
+    int ff[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const Rec64 e = r[1 + j];
+        const int f = feat_of(e.bits);
+        const float x = xs[f * kTileLd + lane];
+        const bool o = satisfies<HAS_NAN>(x, e.lo, e.hi, e.bits);
+        dd[j] = (o ? 1.0 : 0.0) - e.z;
+        zz[j] = e.z;
+        ff[j] = f;
+        cacc[j] = 0.0;
+    }
+    for (int m = 0; m < q.n; ++m) {
+        const double t = q.t[m];
+        double A[D], P[D];
+        P[0] = q.w[m] * val;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            A[j] = fma(t, dd[j], zz[j]);
+            if (j + 1 < D) P[j + 1] = P[j] * A[j];
+        }
+        double S = 1.0;
+#pragma unroll
+        for (int j = D - 1; j >= 0; --j) {
+            cacc[j] += P[j] * S;
+            S *= A[j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) atomicAdd(&ps[ff[j] * kTileLd + lane], dd[j] * cacc[j]);
+}
+
+// --------------------------------------------------------------- kernel ---
+
+template <typename Rec, typename Acc>
+__device__ __forceinline__ size_t fwd_smem_layout(int F, int sub, int D, float** xs, Acc** ps,
+                                                  Rec** stage0, Rec** stage1, uint64_t** bars,
+                                                  unsigned char* base) {
+    const int rows = F + 1;
+    size_t off = 0;
+    *xs = (float*)(base + off);
+    off += (size_t)rows * kTileLd * sizeof(float);
+    off = (off + 15) & ~(size_t)15;
+    *ps = (Acc*)(base + off);
+    off += (size_t)rows * kTileLd * sizeof(Acc);
+    off = (off + 15) & ~(size_t)15;
+    *stage0 = (Rec*)(base + off);
+    off += (size_t)sub * (D + 1) * sizeof(Rec);
+    *stage1 = (Rec*)(base + off);
+    off += (size_t)sub * (D + 1) * sizeof(Rec);
+    off = (off + 15) & ~(size_t)15;
+    *bars = (uint64_t*)(base + off);
+    off += 2 * sizeof(uint64_t);
+    return off;
+}
+
+template <int D, int NP, bool FP64>
+__global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
+    using Rec = typename std::conditional<FP64, Rec64, Rec32>::type;
+    using Acc = typename std::conditional<FP64, double, float>::type;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* xs;
+    Acc* ps;
+    Rec *st0, *st1;
+    uint64_t* bars;
+    fwd_smem_layout<Rec, Acc>(a.F, a.sub, D, &xs, &ps, &st0, &st1, &bars, smem);
+    __shared__ int s_ok;
+
+    const int F = a.F;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int tile = (int)(blockIdx.x % (unsigned)a.n_tiles);
+    const int64_t chunk = blockIdx.x / (unsigned)a.n_tiles;
+    const int64_t s0 = (int64_t)tile * 32;
+    const int64_t p0 = chunk * a.paths_per_block;
+    const int64_t p1 = imin64(p0 + a.paths_per_block, a.n_paths);
+    const int nsub = (int)((p1 - p0 + a.sub - 1) / a.sub);
+    const Rec* rec = (const Rec*)a.rec;
+
+    auto issue = [&](int c) {
+        const int64_t q0 = p0 + (int64_t)c * a.sub;
+        const int cnt = (int)imin64(a.sub, p1 - q0);
+        const uint32_t bytes = (uint32_t)cnt * (D + 1) * (uint32_t)sizeof(Rec);
+        uint64_t* bar = &bars[c & 1];
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_g2s((c & 1) ? (void*)st1 : (void*)st0, rec + q0 * (D + 1), bytes, bar);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < 2 && c < nsub; ++c) issue(c);
+    }
+    // sample tile (transposed: row = feature, column = sample), plus a zero
+    // row F read by padding elements; zero the accumulator tile
+    int nan_seen = 0;
+    for (int idx = threadIdx.x; idx < 32 * F; idx += blockDim.x) {
+        const int s = idx / F, f = idx - s * F;
+        const float v = (s0 + s < a.M) ? a.X[(s0 + s) * F + f] : 0.f;
+        xs[f * kTileLd + s] = v;
+        nan_seen |= (v != v);
+    }
+    for (int idx = threadIdx.x; idx < kTileLd; idx += blockDim.x) xs[F * kTileLd + idx] = 0.f;
+    for (int idx = threadIdx.x; idx < (F + 1) * kTileLd; idx += blockDim.x) ps[idx] = (Acc)0;
+    const bool has_nan = __syncthreads_or(nan_seen) != 0;
+
+    int failed_at = -1;
+    for (int c = 0; c < nsub; ++c) {
+        const uint32_t parity = (uint32_t)((c >> 1) & 1);
+        if (threadIdx.x == 0) s_ok = mbar_wait_bounded(&bars[c & 1], parity) ? 1 : 0;
+        __syncthreads();
+        if (!s_ok) { failed_at = c; break; }
+        (void)mbar_try_wait(&bars[c & 1], parity);  // acquire the bulk-copy writes
+        const Rec* buf = (c & 1) ? st1 : st0;
+        const int cnt = (int)imin64(a.sub, p1 - (p0 + (int64_t)c * a.sub));
+        for (int i = warp; i < cnt; i += nwarps) {
+            const Rec* r = buf + i * (D + 1);
+            if constexpr (FP64) {
+                if (has_nan) fwd_path_f64<D, true>(r, xs, ps, lane, a.qd);
+                else fwd_path_f64<D, false>(r, xs, ps, lane, a.qd);
+            } else {
+                if (has_nan) fwd_path_f32<D, NP, true>(r, xs, ps, lane, a.q);
+                else fwd_path_f32<D, NP, false>(r, xs, ps, lane, a.q);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && c + 2 < nsub) issue(c + 2);
+    }
+    if (failed_at >= 0) {
+        // a bulk copy did not complete in time: record it, wait (bounded) for
+        // the copies still in flight so they cannot land in reused memory, return
+        if (threadIdx.x == 0) {
+            report(a.status, QTS_ERR_TIMEOUT);
+            for (int c = failed_at; c < failed_at + 2 && c < nsub; ++c)
+                (void)mbar_wait_bounded(&bars[c & 1], (uint32_t)((c >> 1) & 1));
+        }
+        return;
+    }
+    for (int idx = threadIdx.x; idx < 32 * F; idx += blockDim.x) {
+        const int s = idx / F, f = idx - s * F;
+        if (s0 + s < a.M) {
+            const Acc v = ps[f * kTileLd + s];
+            if (v != (Acc)0) atomicAdd(&a.phi[(s0 + s) * (F + 1) + f], (double)v);
+        }
+    }
+}
+
+// phi[:, :F] = 0, phi[:, F] = E[f]
+__global__ void phi_init_kernel(double* phi, int64_t M, int F, double bias) {
+    const int64_t n = M * (F + 1);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        phi[i] = (i % (F + 1) == F) ? bias : 0.0;
+}
+
+cudaError_t launch_phi_init(double* phi, int64_t M, int F, double bias, cudaStream_t st) {
+    if (M <= 0) return cudaSuccess;
+    const int64_t n = M * (F + 1);
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4 * 152);
+    phi_init_kernel<<<blocks, 256, 0, st>>>(phi, M, F, bias);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- dispatch ------
+
+template <int D, int NP, bool FP64>
+static cudaError_t launch_fwd_t(const FwdArgs& a, int warps, int64_t blocks, size_t smem,
+                                cudaStream_t st) {
+    auto k = fwd_kernel<D, NP, FP64>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<(unsigned)blocks, warps * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t launch_fwd_d(const FwdArgs& a, int np, bool fp64, int warps, int64_t blocks,
+                                size_t smem, cudaStream_t st) {
+    if (fp64) return launch_fwd_t<D, 2, true>(a, warps, blocks, smem, st);
+    if constexpr (D <= 8) {
+        if (np >= 8) return launch_fwd_t<D, 8, false>(a, warps, blocks, smem, st);
+    }
+    if constexpr (D <= 24) {
+        if (np >= 4) return launch_fwd_t<D, 4, false>(a, warps, blocks, smem, st);
+    }
+    return launch_fwd_t<D, 2, false>(a, warps, blocks, smem, st);
+}
+
+size_t fwd_smem_bytes(int F, int sub, int D, bool fp64) {
+    const size_t rows = F + 1;
+    size_t off = rows * kTileLd * 4;
+    off = (off + 15) & ~(size_t)15;
+    off += rows * kTileLd * (fp64 ? 8 : 4);
+    off = (off + 15) & ~(size_t)15;
+    off += 2 * (size_t)sub * (D + 1) * (fp64 ? sizeof(Rec64) : sizeof(Rec32));
+    off = (off + 15) & ~(size_t)15;
+    return off + 16;
+}
+
+cudaError_t launch_fwd_bucket(const qts_ensemble* e, const Bucket& b, const float* X, int64_t M,
+                              int F, const QuadF& q, const QuadD& qd, double* phi, const Tune& tn,
+                              cudaStream_t st) {
+    if (M <= 0 || b.n_paths == 0) return cudaSuccess;
+    const bool fp64 = (e->flags & QTS_FLAG_FP64) != 0;
+    FwdArgs a;
+    a.rec = fp64 ? (const void*)((const Rec64*)e->d_rec + b.rec_off)
+                 : (const void*)((const Rec32*)e->d_rec + b.rec_off);
+    a.n_paths = b.n_paths;
+    a.sub = std::max(1, tn.sub);
+    a.paths_per_block = std::max<int64_t>(a.sub, (int64_t)tn.paths / a.sub * a.sub);
+    a.n_tiles = (int)((M + 31) / 32);
+    a.X = X;
+    a.M = M;
+    a.F = F;
+    a.phi = phi;
+    a.status = e->d_status;
+    a.q = q;
+    a.qd = qd;
+    const int64_t chunks = (b.n_paths + a.paths_per_block - 1) / a.paths_per_block;
+    const int64_t blocks = chunks * a.n_tiles;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const size_t smem = fwd_smem_bytes(F, a.sub, b.D, fp64);
+    const int warps = std::max(1, std::min(8, tn.warps));
+    switch (b.D) {
+#define QTS_CASE(DD) \
+    case DD: return launch_fwd_d<DD>(a, tn.np, fp64, warps, blocks, smem, st);
+        QTS_CASE(1) QTS_CASE(2) QTS_CASE(3) QTS_CASE(4) QTS_CASE(5) QTS_CASE(6) QTS_CASE(7)
+        QTS_CASE(8) QTS_CASE(9) QTS_CASE(10) QTS_CASE(11) QTS_CASE(12) QTS_CASE(13) QTS_CASE(14)
+        QTS_CASE(15) QTS_CASE(16) QTS_CASE(20) QTS_CASE(24) QTS_CASE(28) QTS_CASE(32)
+        QTS_CASE(40) QTS_CASE(48) QTS_CASE(56) QTS_CASE(64)
+#undef QTS_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace qts

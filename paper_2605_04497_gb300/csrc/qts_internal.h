@@ -1,0 +1,168 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qtreeshap.h"
+
+namespace qts {
+
+// ---------------------------------------------------------------- records --
+//
+// FP32 path table of a bucket of width D: each path occupies D+1 consecutive
+// 16-byte records.  Record 0 is the header {val, prod_j z_j, 0, 0}; records
+// 1..D are the merged elements {z, lo, hi, bits} with bits = feature index
+// (low 24 bits) | NaN-satisfies flag (bit 31).  Paths with d < D unique
+// features are padded with neutral elements {1, -inf, +inf, F | NaN-ok}:
+// a = 1 at every node and o - z = 0, so they add nothing.  Elements are sorted
+// by feature index, so element order = feature order (used by interactions).
+struct __align__(16) Rec32 {
+    float z, lo, hi;
+    uint32_t bits;
+};
+constexpr uint32_t kNanOk = 0x80000000u;
+constexpr uint32_t kFeatMask = 0x00FFFFFFu;
+
+// FP64 table: 32-byte records {z, 0, lo, hi, bits, 0}; header {val, prod z}.
+struct __align__(16) Rec64 {
+    double z;
+    double aux;
+    float lo, hi;
+    uint32_t bits;
+    uint32_t pad;
+};
+
+constexpr int kMaxBuckets = 32;
+constexpr int kMaxD = QTS_MAX_UNIQUE_FEATURES_PER_PATH;
+
+// bucket widths: exact up to 16 unique features, then steps of 4 and 8
+int bucket_width_for(int d);
+
+struct Bucket {
+    int D = 0;              // record width (unique features, padded)
+    int64_t n_paths = 0;
+    int64_t rec_off = 0;    // first record (Rec32 or Rec64 units) in d_rec
+    int64_t path_base = 0;  // global path index of the first path
+    int64_t slot_base = 0;  // global element slot of the first element (n_paths * D slots)
+};
+
+// Host result of path preparation (Sec. 2 merging).
+struct Prepared {
+    std::vector<Bucket> buckets;
+    std::vector<Rec32> rec32;     // FP32 tables, all buckets back to back
+    std::vector<Rec64> rec64;     // FP64 tables (QTS_FLAG_FP64 only)
+    std::vector<int64_t> path_leaf;   // per global path: leaf node (global index)
+    std::vector<double> path_zprod;   // per global path: prod_j z_j (fp64)
+    std::vector<double> path_val;     // per global path: leaf value
+    std::vector<int64_t> slot_edge_begin;  // per element slot + 1: CSR into edge arrays
+    std::vector<int64_t> edge_node;        // global node index of the merged edge
+    std::vector<double> edge_coef;         // prod of the other edge weights in the element
+    std::vector<int64_t> empty_leaf;       // leaves of single-leaf trees (no split)
+    std::vector<double> empty_val;
+    int64_t n_paths = 0, n_slots = 0, n_leaves = 0, sum_unique = 0;
+    int max_unique = 0;
+    double bias = 0.0;  // E[f]
+};
+
+// Prepare the path tables (host, multi-threaded).  Returns QTS_OK or an error
+// with the message in *err.
+qts_status prepare(int32_t n_trees, const int64_t* off, const int32_t* left, const int32_t* right,
+                   const int32_t* feature, const float* thr, const uint8_t* defl, const float* z,
+                   const float* leaf, int32_t F, bool fp64, Prepared* out, std::string* err);
+
+// Gauss-Legendre nodes on [0,1] (Golub-Welsch via Jacobi eigen-decomposition).
+bool gauss_legendre(int n, double* t, double* w);
+
+// Launch tuning of one bucket width.
+struct Tune {
+    int warps = 4;        // warps per block (samples are shared, paths split)
+    int paths = 128;      // paths per block (chunk)
+    int sub = 32;         // paths per staged sub-chunk
+    int np = 8;           // nodes per register pass (8, 4 or 2)
+};
+
+}  // namespace qts
+
+// The opaque handle.
+struct qts_ensemble {
+    int32_t n_trees = 0, n_features = 0;
+    int64_t n_nodes = 0;
+    uint32_t flags = 0;
+    int device = 0;
+    // host copy of the model (for qts_update_params)
+    std::vector<int64_t> off;
+    std::vector<int32_t> left, right, feature;
+    std::vector<float> thr, z, leaf;
+    std::vector<uint8_t> defl;
+    // prepared tables
+    qts::Prepared prep;
+    // device memory
+    void* d_rec = nullptr;            // Rec32 or Rec64 tables
+    int64_t* d_path_leaf = nullptr;   // n_paths
+    double* d_path_zprod = nullptr;   // n_paths
+    int64_t* d_slot_edge_begin = nullptr;  // n_slots + 1
+    int64_t* d_edge_node = nullptr;
+    double* d_edge_coef = nullptr;
+    int64_t* d_empty_leaf = nullptr;
+    int* d_status = nullptr;          // device status word
+    int64_t device_bytes = 0;
+    // grow-only workspace (interaction accumulators, adjoint per-path sums)
+    void* d_work = nullptr;
+    size_t work_bytes = 0;
+    // per-width launch tuning (index = bucket width)
+    qts::Tune tune[qts::kMaxD + 1];
+    bool tuned = false;
+};
+
+namespace qts {
+
+void set_error(const std::string& msg);
+qts_status fail(qts_status st, const std::string& msg);
+qts_status cuda_fail(cudaError_t e, const char* what);
+qts_status ensure_workspace(qts_ensemble* e, size_t bytes);
+qts_status upload(qts_ensemble* e);
+void release_device(qts_ensemble* e);
+int num_sms();
+
+// GL nodes packed for the kernels (fp32 and fp64), padded to a multiple of 8
+// with zero-weight nodes at t = 1/2.
+struct QuadF {
+    float t[QTS_MAX_QUAD + 8];
+    float w[QTS_MAX_QUAD + 8];
+    int n, n_pad;
+};
+struct QuadD {
+    double t[QTS_MAX_QUAD + 8];
+    double w[QTS_MAX_QUAD + 8];
+    int n, n_pad;
+};
+bool make_quad(int n, QuadF* qf, QuadD* qd);
+
+// validate common call arguments
+qts_status check_call(qts_ensemble* e, const float* X, int64_t M, int32_t F, int32_t n_quad);
+
+// ----------------------------------------------------- kernel launchers ---
+// (defined in the .cu files; all enqueue on `st` and return cudaGetLastError)
+
+cudaError_t launch_phi_init(double* phi, int64_t M, int F, double bias, cudaStream_t st);
+cudaError_t launch_fwd_bucket(const qts_ensemble* e, const Bucket& b, const float* X, int64_t M,
+                              int F, const QuadF& q, const QuadD& qd, double* phi, const Tune& tn,
+                              cudaStream_t st);
+cudaError_t launch_int_bucket(const qts_ensemble* e, const Bucket& b, const float* X, int64_t M,
+                              int F, const QuadF& q, double* acc_pair, double* acc_phi,
+                              cudaStream_t st);
+cudaError_t launch_int_finalize(const double* acc_pair, const double* acc_phi, int64_t M, int F,
+                                double bias, float* out, cudaStream_t st);
+cudaError_t launch_bwd_bucket(const qts_ensemble* e, const Bucket& b, const float* X,
+                              const float* grad, int64_t M, int F, const QuadF& q,
+                              double* g_val, double* g_slot, double* phi, const Tune& tn,
+                              cudaStream_t st);
+cudaError_t launch_bwd_epilogue(const qts_ensemble* e, const float* grad, int64_t M, int F,
+                                const double* g_val, const double* g_slot, double* d_leaf,
+                                double* d_z, double* g_bias_scratch, cudaStream_t st);
+
+}  // namespace qts

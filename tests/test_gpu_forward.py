@@ -1,0 +1,177 @@
+"""GPU parity of the first-order path (qts_shap_values) against the FP64 oracle.
+
+Tolerance (stated by the target): per sample,
+    max_i |phi_gpu - phi_oracle| / max(|f(x)|, max_i |phi_oracle_i|) <= 1e-5
+for the FP32 kernels and <= 1e-12 for QTS_FLAG_FP64.  The normaliser adds
+max|phi_i| to |f(x)| because |f(x)| alone is fragile when a prediction is ~0.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import golden_trees, rel_err_rows, sample_x, tiny_ensemble
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def qts():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_04497_gb300 import build as b
+
+    b.build()
+    import paper_2605_04497_gb300 as q
+
+    return q
+
+
+def run_gpu(q, ens, X, n_quad=8, fp64=False):
+    import torch
+
+    E = q.Ensemble.from_arrays(ens, fp64=fp64)
+    Xd = torch.from_numpy(np.ascontiguousarray(X, np.float32)).cuda()
+    phi = q.shap_values(E, Xd, n_quad)
+    E.sync_status()
+    out = phi.cpu().numpy()
+    E.close()
+    return out
+
+
+def test_golden_trees_on_gpu(qts):
+    for spec, ens in golden_trees():
+        X = np.stack([sample_x(s) for s in spec["samples"]])
+        got = run_gpu(qts, ens, X)
+        want = np.array([s["phi"] for s in spec["samples"]])
+        assert np.abs(got - want).max() < 1e-6
+
+
+def test_config0_full(qts):
+    w = synth.single_config(0)  # M = 100: three full tiles and a ragged one
+    ref = oracle.shap_exact(w.ens, w.X)
+    got = run_gpu(qts, w.ens, w.X)
+    assert rel_err_rows(got, ref).max() <= TOL32
+    assert np.abs(got[:, -1] - ref[:, -1]).max() < 1e-12  # bias is fp64 on both sides
+
+
+def test_config0_fp64_mode(qts):
+    w = synth.single_config(0)
+    ref = oracle.shap_exact(w.ens, w.X)
+    got = run_gpu(qts, w.ens, w.X, fp64=True)
+    assert rel_err_rows(got, ref).max() <= TOL64
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_repeated_features_many_buckets(qts, seed):
+    """Depth 12 on 7 features: merged paths of every width 1..7, several buckets."""
+    ens = tiny_ensemble(300 + seed, n_trees=20, depth=12, F=7, n_train=5000)
+    X = synth.normal(300 + seed, 1, (77, 7))
+    ref = oracle.shap_exact(ens, X)
+    got = run_gpu(qts, ens, X)
+    assert rel_err_rows(got, ref).max() <= TOL32
+
+
+def test_wide_paths_up_to_32(qts):
+    """Paths with up to ~30 unique features exercise the 20..32 buckets; 16 points
+    are exact for d <= 32 (Thm 2), so the FP64 mode must match the exact oracle."""
+    ens = tiny_ensemble(401, n_trees=4, depth=30, F=40, n_train=3000)
+    _, dmax, _ = oracle.path_stats(ens)
+    assert dmax > 16
+    X = synth.normal(401, 1, (40, 40))
+    ref = oracle.shap_exact(ens, X)
+    got = run_gpu(qts, ens, X, n_quad=16)
+    assert rel_err_rows(got, ref).max() <= TOL32
+    got64 = run_gpu(qts, ens, X, n_quad=16, fp64=True)
+    assert rel_err_rows(got64, ref).max() <= TOL64
+
+
+@pytest.mark.parametrize("n_quad", [1, 3, 5, 8, 16])
+def test_n_quad_matches_oracle_quadrature(qts, n_quad):
+    """With n points the kernel computes the n-point rule (Eq.
+    shap_as_weighted_banzhafs), exact or not; compare with the oracle's rule."""
+    ens = tiny_ensemble(501, n_trees=10, depth=10, F=12, n_train=4000)
+    X = synth.normal(501, 1, (45, 12))
+    ref = oracle.shap_quad(ens, X, n_quad)
+    got = run_gpu(qts, ens, X, n_quad=n_quad)
+    assert rel_err_rows(got, ref).max() <= TOL32
+    got64 = run_gpu(qts, ens, X, n_quad=n_quad, fp64=True)
+    assert rel_err_rows(got64, ref).max() <= TOL64
+
+
+def test_missing_values(qts):
+    ens = tiny_ensemble(601, n_trees=8, depth=6, F=6, n_train=2000)
+    X = synth.normal(601, 1, (64, 6))
+    X[::3, 2] = np.nan
+    X[5, :] = np.nan
+    X[40:, 0] = np.nan
+    ref = oracle.shap_exact(ens, X)
+    got = run_gpu(qts, ens, X)
+    assert rel_err_rows(got, ref).max() <= TOL32
+    f = oracle.predict(ens, X)
+    assert np.abs(got.sum(axis=1) - f).max() <= TOL32 * max(1.0, np.abs(f).max())
+
+
+def test_edge_sizes(qts):
+    import torch
+
+    w = synth.single_config(0)
+    for M in (1, 31, 32, 33):
+        ref = oracle.shap_exact(w.ens, w.X[:M])
+        got = run_gpu(qts, w.ens, w.X[:M])
+        assert got.shape == (M, 9) and rel_err_rows(got, ref).max() <= TOL32
+    E = qts.Ensemble.from_arrays(w.ens)
+    X0 = torch.zeros((0, 8), dtype=torch.float32, device="cuda")
+    out = qts.shap_values(E, X0)
+    assert out.shape == (0, 9)
+    with pytest.raises(qts.QtsError):
+        qts.shap_values(E, torch.zeros((4, 8), device="cuda"), n_quad=0)
+    E.close()
+
+
+def test_single_leaf_tree_only_adds_bias(qts):
+    spec, ens = golden_trees()[0]
+    stump = synth.Ensemble([0, 1], [-1], [-1], [-1], [0], [0], [1], [2.5], [1], 2)
+    both = synth.concat([ens, stump])
+    X = np.stack([sample_x(s) for s in spec["samples"]])
+    got = run_gpu(qts, both, X)
+    want = np.array([s["phi"] for s in spec["samples"]])
+    want[:, -1] += 2.5
+    assert np.abs(got - want).max() < 1e-6
+
+
+def test_config1_full_size_sampled_rows(qts):
+    """configs[1] at full size (1000 trees, M = 10,000) in the launch
+    configuration the benchmark uses; the oracle checks a sample of rows."""
+    import torch
+
+    w = synth.single_config(1)
+    E = qts.Ensemble.from_arrays(w.ens)
+    Xd = torch.from_numpy(w.X).cuda()
+    phi = qts.shap_values(E, Xd).cpu().numpy()
+    E.sync_status()
+    rows = np.r_[0:8, 4999:5003, 9990:10000]
+    ref = oracle.shap_exact(w.ens, w.X[rows])
+    assert rel_err_rows(phi[rows], ref).max() <= TOL32
+    f = oracle.predict(w.ens, w.X)
+    assert np.abs(phi.sum(axis=1) - f).max() <= TOL32 * max(1.0, np.abs(f).max())
+    E.close()
+
+
+def test_config2_deep_trees_sampled(qts):
+    """configs[2] shape (depth 20, repeated features): 8 points vs the exact
+    expansion; paths beyond 16 unique features carry quadrature error (Thm 2)."""
+    import torch
+
+    w = synth.single_config(2, n_samples=256, n_trees=20)
+    E = qts.Ensemble.from_arrays(w.ens)
+    phi = qts.shap_values(E, torch.from_numpy(w.X).cuda()).cpu().numpy()
+    E.sync_status()
+    ref = oracle.shap_exact(w.ens, w.X[:24])
+    assert rel_err_rows(phi[:24], ref).max() <= TOL32
+    E.close()
