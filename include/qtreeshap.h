@@ -81,7 +81,9 @@ typedef enum qts_status {
  *   feature            host, split feature in [0, n_features) (ignored at leaves)
  *   threshold          host, fp32 split value
  *   default_left       host, 1 if NaN goes left (may be NULL: NaN goes left)
- *   z                  host, edge weight into the node, 0 < z <= 1 (root ignored)
+ *   z                  host, edge weight into the node (root ignored); a cover
+ *                      fraction in (0, 1], but any positive finite value is
+ *                      accepted so that refits may move it
  *   leaf_value         host, value at leaves (ignored at internal nodes)
  *   n_features         number of features F, 1..QTS_MAX_FEATURES
  *   flags              0 or QTS_FLAG_FP64

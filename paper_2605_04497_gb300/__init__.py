@@ -288,6 +288,8 @@ class QTreeShapFn:
                             np.array_equal(zz, ens._host["z"])):
                         ens.update_params(zz, lv)
                     ctx.ens, ctx.n_quad = ens, n_quad
+                    ctx.dev_l, ctx.dev_z = leaf_values.device, z.device
+                    ctx.dt_l, ctx.dt_z = leaf_values.dtype, z.dtype
                     ctx.save_for_backward(X)
                     return shap_values(ens, X, n_quad)
 
@@ -296,7 +298,8 @@ class QTreeShapFn:
                     (X,) = ctx.saved_tensors
                     g = grad_phi.to(torch.float32).contiguous()
                     d_leaf, d_z = shap_backward(ctx.ens, X, g, ctx.n_quad)
-                    return d_leaf.to(torch.float32), d_z.to(torch.float32), None, None, None
+                    return (d_leaf.to(device=ctx.dev_l, dtype=ctx.dt_l),
+                            d_z.to(device=ctx.dev_z, dtype=ctx.dt_z), None, None, None)
 
             cls._fn = _F
         return cls._fn.apply(leaf_values, z, X, ens, n_quad)

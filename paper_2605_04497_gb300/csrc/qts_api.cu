@@ -47,6 +47,8 @@ void release_device(qts_ensemble* e) {
     cudaFree(e->d_rec);
     cudaFree(e->d_path_leaf);
     cudaFree(e->d_path_zprod);
+    cudaFree(e->d_path_val);
+    cudaFree(e->d_slot_zexcl);
     cudaFree(e->d_slot_edge_begin);
     cudaFree(e->d_edge_node);
     cudaFree(e->d_edge_coef);
@@ -54,6 +56,8 @@ void release_device(qts_ensemble* e) {
     e->d_rec = nullptr;
     e->d_path_leaf = nullptr;
     e->d_path_zprod = nullptr;
+    e->d_path_val = nullptr;
+    e->d_slot_zexcl = nullptr;
     e->d_slot_edge_begin = nullptr;
     e->d_edge_node = nullptr;
     e->d_edge_coef = nullptr;
@@ -82,6 +86,8 @@ qts_status upload(qts_ensemble* e) {
     else st = up((Rec32**)&e->d_rec, P.rec32, &tot, "upload path tables");
     if (st == QTS_OK) st = up(&e->d_path_leaf, P.path_leaf, &tot, "upload path leaves");
     if (st == QTS_OK) st = up(&e->d_path_zprod, P.path_zprod, &tot, "upload path products");
+    if (st == QTS_OK) st = up(&e->d_path_val, P.path_val, &tot, "upload path values");
+    if (st == QTS_OK) st = up(&e->d_slot_zexcl, P.slot_zexcl, &tot, "upload element products");
     if (st == QTS_OK) st = up(&e->d_slot_edge_begin, P.slot_edge_begin, &tot, "upload element edges");
     if (st == QTS_OK) st = up(&e->d_edge_node, P.edge_node, &tot, "upload edge nodes");
     if (st == QTS_OK) st = up(&e->d_edge_coef, P.edge_coef, &tot, "upload edge coefficients");

@@ -95,3 +95,82 @@ __device__ __forceinline__ bool satisfies(float x, float lo, float hi, uint32_t 
 }
 
 }  // namespace qts
+
+namespace qts {
+
+// Block-level path streaming.  The block's path range [p0, p1) of one bucket
+// (D elements + 1 header record per path) is copied into two shared staging
+// buffers of `sub` paths each by bulk copies, double-buffered on two
+// mbarriers; warp w calls body(global_path_index, records) for paths
+// w, w + nwarps, ... of each staged sub-chunk.  Thread 0 does the bounded wait
+// and broadcasts the outcome, so the decision to stop is block-uniform.
+// Returns false (after reporting QTS_ERR_TIMEOUT and waiting, bounded, for the
+// copies in flight) if a copy did not complete.  Must be called by all threads;
+// `bars` must have been initialised by mbar_init(.., 1) and a __syncthreads.
+template <typename Rec, int D, typename Body>
+__device__ __forceinline__ bool stream_paths(const Rec* __restrict__ rec, int64_t p0, int64_t p1, int sub,
+                                             Rec* st0, Rec* st1, uint64_t* bars, uint32_t* phase_base,
+                                             int* s_flag, int* status, Body&& body) {
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int nsub = (int)((p1 - p0 + sub - 1) / sub);
+    // phase_base[k] counts completed phases of barrier k before this call, so
+    // the driver can be called repeatedly (persistent kernels) on the same bars
+    auto issue = [&](int c) {
+        const int64_t q0 = p0 + (int64_t)c * sub;
+        const int cnt = (int)imin64(sub, p1 - q0);
+        const uint32_t bytes = (uint32_t)cnt * (D + 1) * (uint32_t)sizeof(Rec);
+        uint64_t* bar = &bars[c & 1];
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_g2s((c & 1) ? (void*)st1 : (void*)st0, rec + q0 * (D + 1), bytes, bar);
+    };
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 2 && c < nsub; ++c) issue(c);
+    int failed_at = -1;
+    for (int c = 0; c < nsub; ++c) {
+        const uint32_t parity = (phase_base[c & 1] + (uint32_t)(c >> 1)) & 1u;
+        if (threadIdx.x == 0) *s_flag = mbar_wait_bounded(&bars[c & 1], parity) ? 1 : 0;
+        __syncthreads();
+        if (!*s_flag) { failed_at = c; break; }
+        (void)mbar_try_wait(&bars[c & 1], parity);  // acquire the bulk-copy writes
+        const Rec* buf = (c & 1) ? st1 : st0;
+        const int64_t q0 = p0 + (int64_t)c * sub;
+        const int cnt = (int)imin64(sub, p1 - q0);
+        for (int i = warp; i < cnt; i += nwarps) body(q0 + i, buf + i * (D + 1));
+        __syncthreads();
+        if (threadIdx.x == 0 && c + 2 < nsub) issue(c + 2);
+    }
+    if (failed_at >= 0) {
+        if (threadIdx.x == 0) {
+            report(status, QTS_ERR_TIMEOUT);
+            for (int c = failed_at; c < failed_at + 2 && c < nsub; ++c)
+                (void)mbar_wait_bounded(&bars[c & 1], (phase_base[c & 1] + (uint32_t)(c >> 1)) & 1u);
+        }
+        __syncthreads();
+        return false;
+    }
+    // advance the phase counters by the number of copies each barrier completed
+    if (threadIdx.x == 0) {
+        phase_base[0] += (uint32_t)((nsub + 1) / 2);
+        phase_base[1] += (uint32_t)(nsub / 2);
+    }
+    __syncthreads();
+    return true;
+}
+
+// Transposed tile of 32 rows of a row-major matrix: tile[c * kTileLd + s] =
+// A[(s0 + s) * ld + c] for c < ncols (0 beyond M), plus `extra` zero rows.
+// Returns (block-wide) whether any loaded value is NaN.
+__device__ __forceinline__ bool load_tile_t(float* tile, const float* __restrict__ A, int64_t s0,
+                                            int64_t M, int ncols, int64_t ld, int extra) {
+    int nan_seen = 0;
+    for (int idx = threadIdx.x; idx < 32 * ncols; idx += blockDim.x) {
+        const int s = idx / ncols, c = idx - s * ncols;
+        const float v = (s0 + s < M) ? A[(s0 + s) * ld + c] : 0.f;
+        tile[c * kTileLd + s] = v;
+        nan_seen |= (v != v);
+    }
+    for (int idx = threadIdx.x; idx < extra * kTileLd; idx += blockDim.x) tile[ncols * kTileLd + idx] = 0.f;
+    return __syncthreads_or(nan_seen) != 0;
+}
+
+}  // namespace qts

@@ -164,59 +164,30 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
     Rec *st0, *st1;
     uint64_t* bars;
     fwd_smem_layout<Rec, Acc>(a.F, a.sub, D, &xs, &ps, &st0, &st1, &bars, smem);
-    __shared__ int s_ok;
+    __shared__ int s_flag;
+    __shared__ uint32_t s_phase[2];
 
     const int F = a.F;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int tile = (int)(blockIdx.x % (unsigned)a.n_tiles);
     const int64_t chunk = blockIdx.x / (unsigned)a.n_tiles;
     const int64_t s0 = (int64_t)tile * 32;
     const int64_t p0 = chunk * a.paths_per_block;
     const int64_t p1 = imin64(p0 + a.paths_per_block, a.n_paths);
-    const int nsub = (int)((p1 - p0 + a.sub - 1) / a.sub);
-    const Rec* rec = (const Rec*)a.rec;
 
-    auto issue = [&](int c) {
-        const int64_t q0 = p0 + (int64_t)c * a.sub;
-        const int cnt = (int)imin64(a.sub, p1 - q0);
-        const uint32_t bytes = (uint32_t)cnt * (D + 1) * (uint32_t)sizeof(Rec);
-        uint64_t* bar = &bars[c & 1];
-        mbar_arrive_expect_tx(bar, bytes);
-        bulk_g2s((c & 1) ? (void*)st1 : (void*)st0, rec + q0 * (D + 1), bytes, bar);
-    };
     if (threadIdx.x == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         mbar_fence_init();
+        s_phase[0] = s_phase[1] = 0;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int c = 0; c < 2 && c < nsub; ++c) issue(c);
-    }
-    // sample tile (transposed: row = feature, column = sample), plus a zero
-    // row F read by padding elements; zero the accumulator tile
-    int nan_seen = 0;
-    for (int idx = threadIdx.x; idx < 32 * F; idx += blockDim.x) {
-        const int s = idx / F, f = idx - s * F;
-        const float v = (s0 + s < a.M) ? a.X[(s0 + s) * F + f] : 0.f;
-        xs[f * kTileLd + s] = v;
-        nan_seen |= (v != v);
-    }
-    for (int idx = threadIdx.x; idx < kTileLd; idx += blockDim.x) xs[F * kTileLd + idx] = 0.f;
     for (int idx = threadIdx.x; idx < (F + 1) * kTileLd; idx += blockDim.x) ps[idx] = (Acc)0;
-    const bool has_nan = __syncthreads_or(nan_seen) != 0;
+    // sample tile (row = feature, column = sample) plus a zero row F for padding
+    const bool has_nan = load_tile_t(xs, a.X, s0, a.M, F, F, 1);
 
-    int failed_at = -1;
-    for (int c = 0; c < nsub; ++c) {
-        const uint32_t parity = (uint32_t)((c >> 1) & 1);
-        if (threadIdx.x == 0) s_ok = mbar_wait_bounded(&bars[c & 1], parity) ? 1 : 0;
-        __syncthreads();
-        if (!s_ok) { failed_at = c; break; }
-        (void)mbar_try_wait(&bars[c & 1], parity);  // acquire the bulk-copy writes
-        const Rec* buf = (c & 1) ? st1 : st0;
-        const int cnt = (int)imin64(a.sub, p1 - (p0 + (int64_t)c * a.sub));
-        for (int i = warp; i < cnt; i += nwarps) {
-            const Rec* r = buf + i * (D + 1);
+    const bool ok = stream_paths<Rec, D>(
+        (const Rec*)a.rec, p0, p1, a.sub, st0, st1, bars, s_phase, &s_flag, a.status,
+        [&](int64_t, const Rec* r) {
             if constexpr (FP64) {
                 if (has_nan) fwd_path_f64<D, true>(r, xs, ps, lane, a.qd);
                 else fwd_path_f64<D, false>(r, xs, ps, lane, a.qd);
@@ -224,20 +195,8 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
                 if (has_nan) fwd_path_f32<D, NP, true>(r, xs, ps, lane, a.q);
                 else fwd_path_f32<D, NP, false>(r, xs, ps, lane, a.q);
             }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0 && c + 2 < nsub) issue(c + 2);
-    }
-    if (failed_at >= 0) {
-        // a bulk copy did not complete in time: record it, wait (bounded) for
-        // the copies still in flight so they cannot land in reused memory, return
-        if (threadIdx.x == 0) {
-            report(a.status, QTS_ERR_TIMEOUT);
-            for (int c = failed_at; c < failed_at + 2 && c < nsub; ++c)
-                (void)mbar_wait_bounded(&bars[c & 1], (uint32_t)((c >> 1) & 1));
-        }
-        return;
-    }
+        });
+    if (!ok) return;
     for (int idx = threadIdx.x; idx < 32 * F; idx += blockDim.x) {
         const int s = idx / F, f = idx - s * F;
         if (s0 + s < a.M) {

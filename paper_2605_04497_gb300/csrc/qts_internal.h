@@ -58,6 +58,7 @@ struct Prepared {
     std::vector<int64_t> path_leaf;   // per global path: leaf node (global index)
     std::vector<double> path_zprod;   // per global path: prod_j z_j (fp64)
     std::vector<double> path_val;     // per global path: leaf value
+    std::vector<double> slot_zexcl;        // per element slot: prod_{l != j} z_l of its path
     std::vector<int64_t> slot_edge_begin;  // per element slot + 1: CSR into edge arrays
     std::vector<int64_t> edge_node;        // global node index of the merged edge
     std::vector<double> edge_coef;         // prod of the other edge weights in the element
@@ -104,6 +105,8 @@ struct qts_ensemble {
     void* d_rec = nullptr;            // Rec32 or Rec64 tables
     int64_t* d_path_leaf = nullptr;   // n_paths
     double* d_path_zprod = nullptr;   // n_paths
+    double* d_path_val = nullptr;     // n_paths
+    double* d_slot_zexcl = nullptr;   // n_slots
     int64_t* d_slot_edge_begin = nullptr;  // n_slots + 1
     int64_t* d_edge_node = nullptr;
     double* d_edge_coef = nullptr;

@@ -5,16 +5,6 @@ using namespace qts;
 
 extern "C" {
 
-qts_status qts_shap_interactions(qts_ensemble*, const float*, int64_t, int32_t, int32_t, float*,
-                                 qts_stream_t) {
-    return fail(QTS_ERR_UNSUPPORTED, "qts_shap_interactions is not built yet");
-}
-
-qts_status qts_shap_backward(qts_ensemble*, const float*, int64_t, int32_t, int32_t, const float*,
-                             double*, double*, qts_stream_t) {
-    return fail(QTS_ERR_UNSUPPORTED, "qts_shap_backward is not built yet");
-}
-
 qts_status qts_batched_fwd_bwd(int32_t, const qts_request*, int32_t, qts_stream_t) {
     return fail(QTS_ERR_UNSUPPORTED, "qts_batched_fwd_bwd is not built yet");
 }

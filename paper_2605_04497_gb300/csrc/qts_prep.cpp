@@ -272,8 +272,8 @@ static qts_status validate(int32_t n_trees, const int64_t* off, const int32_t* l
                 if (std::isnan(thr[g])) { *err = "NaN threshold at node " + std::to_string(g); return QTS_ERR_ARG; }
                 for (int32_t c : {l, r}) {
                     float zc = z[a + c];
-                    if (!(zc > 0.f && zc <= 1.f)) {
-                        *err = "edge weight z must be in (0, 1] at node " + std::to_string(a + c);
+                    if (!(zc > 0.f && std::isfinite(zc))) {
+                        *err = "edge weight z must be positive and finite at node " + std::to_string(a + c);
                         return QTS_ERR_ARG;
                     }
                 }
@@ -353,6 +353,7 @@ qts_status prepare(int32_t n_trees, const int64_t* off, const int32_t* left, con
     P->path_zprod.resize((size_t)path_total);
     P->path_val.resize((size_t)path_total);
     P->slot_edge_begin.assign((size_t)slot_total + 1, 0);
+    P->slot_zexcl.assign((size_t)slot_total, 0.0);
 
     // fill, bucket by bucket in tree order; first count edges per slot
     std::vector<int64_t> cursor(P->buckets.size());
@@ -396,8 +397,13 @@ qts_status prepare(int32_t n_trees, const int64_t* off, const int32_t* left, con
                 }
             }
             int64_t slot0 = b.slot_base + lp * D;
-            for (int j = 0; j < p.d; ++j)
+            for (int j = 0; j < p.d; ++j) {
                 P->slot_edge_begin[slot0 + j + 1] = o.elems[p.el_off + j].edge_cnt;
+                double ex = 1.0;  // prod of the other elements' z (no division)
+                for (int l = 0; l < p.d; ++l)
+                    if (l != j) ex *= o.elems[p.el_off + l].z;
+                P->slot_zexcl[slot0 + j] = ex;
+            }
         }
     }
     for (int64_t s = 0; s < slot_total; ++s) P->slot_edge_begin[s + 1] += P->slot_edge_begin[s];
