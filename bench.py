@@ -1,0 +1,417 @@
+"""Benchmark: batched forward + adjoint Path-Dependent SHAP on a heterogeneous
+batch of 64 tree ensembles, on GB300.
+
+One step = one graph launch of the persistent batched kernel that computes, for
+all 64 requests, phi (M x (F+1)) and the adjoint d/d(leaf values), d/d(edge
+weights) of sum(grad_phi * phi), with inputs resident in HBM.  The metric is
+sample*trees/s (sum over requests of M * trees per step time).  Alongside: the
+plain per-ensemble kernels (forward + adjoint launched per request), the
+persistent kernel's FP32-pipe roofline fraction, an end-to-end figure through
+the C ABI with host buffers, and the FP64 CPU oracle timed on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+N > 1 (torchrun): replicas, each rank runs the whole batch ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SHAP sample·trees/s, batched fwd+bwd vs plain kernel at rel err ≤1e-5; FMA %"
+UNIT = "sample·trees/s"
+WORKLOAD = ("batch64: 64 ensembles, trees log-U[10,2000], depth U{3..16}, F log-U[8,200], "
+            "M log-U[1,50000], covers from min(100000, 20*2^depth) rows, grad_phi ~N(0,1), seed 20260504")
+N_QUAD = 8
+# FP32-pipe operations per (sample, merged path element, quadrature node)
+OPS_FUSED = 11   # forward + adjoint in one pass
+OPS_FWD = 4      # forward alone
+OPS_BWD = 11     # adjoint alone (plain kernel)
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def fp32_peak_tops(sms: int, mhz: float) -> float:
+    """FP32 pipe lane-operations per second: SMs x 128 lanes x clock."""
+    return sms * 128 * mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.remove(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ workload
+
+def make_workload():
+    import synth
+
+    t0 = time.time()
+    works = synth.batch_config()
+    log(f"generated {len(works)} ensembles in {time.time() - t0:.1f}s")
+    return works
+
+
+def units(works):
+    return int(sum(w.M * w.ens.n_trees for w in works))
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    import paper_2605_04497_gb300 as qts
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    works = make_workload()
+    t0 = time.time()
+    ens = [qts.Ensemble.from_arrays(w.ens) for w in works]
+    log(f"prepared path tables in {time.time() - t0:.1f}s")
+    infos = [e.info() for e in ens]
+    X = [torch.from_numpy(w.X).to(dev) for w in works]
+    G = [torch.from_numpy(w.grad_phi).to(dev) for w in works]
+    phi = [torch.empty((w.M, w.F + 1), dtype=torch.float64, device=dev) for w in works]
+    dl = [torch.empty(e.n_nodes, dtype=torch.float64, device=dev) for e in ens]
+    dz = [torch.empty(e.n_nodes, dtype=torch.float64, device=dev) for e in ens]
+    items = [dict(ens=e, X=x, grad_phi=g, phi=p, d_leaf=a, d_z=b)
+             for e, x, g, p, a, b in zip(ens, X, G, phi, dl, dz)]
+    reqs = qts.make_requests(items)
+    U = units(works)
+    elem_nodes = sum(w.M * info["sum_unique"] for w, info in zip(works, infos)) * N_QUAD
+    alg_ops = elem_nodes * OPS_FUSED
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    def step():
+        qts.batched_fwd_bwd(reqs, N_QUAD)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for e in ens:
+        e.sync_status()
+    n_kern = qts.batched_kernel_count()
+
+    # timed region: K steps, L2 flushed between steps (outside the events)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kern_ms = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.time()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        try:
+            kern_ms.append(qts.batched_last_kernel_ms())
+        except qts.QtsError:
+            kern_ms.append(None)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    wall = time.time() - wall0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = U * world / (ms / 1e3)
+    if all(k is not None for k in kern_ms):
+        kms, kms_src = float(np.mean(kern_ms)), "CUDA events around the persistent kernel inside the graph"
+    else:  # conservative: the whole step (init + persistent kernel + epilogues)
+        kms, kms_src = float(np.mean(step_ms)), "CUDA events around the whole step"
+
+    out = None
+    if rank == 0:
+        # plain per-ensemble kernels: forward and adjoint launched per request
+        def plain():
+            for it in items:
+                qts.shap_values(it["ens"], it["X"], N_QUAD, out=it["phi"])
+                qts.shap_backward(it["ens"], it["X"], it["grad_phi"], N_QUAD)
+        plain()
+        torch.cuda.synchronize()
+        pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+        for a, b in pe:
+            flush.fill_(1.0)
+            a.record(stream)
+            plain()
+            b.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = float(np.mean([a.elapsed_time(b) for a, b in pe]))
+
+        # end to end through the C ABI with host buffers: H2D of X and grad_phi
+        # from pinned memory, the batched call, D2H of phi and both gradients
+        hX = [x.cpu().pin_memory() for x in X]
+        hG = [g.cpu().pin_memory() for g in G]
+        hphi = [p.cpu().pin_memory() for p in phi]
+        hdl = [a.cpu().pin_memory() for a in dl]
+        hdz = [a.cpu().pin_memory() for a in dz]
+        h2d = sum(t.numel() * t.element_size() for t in hX + hG)
+        d2h = sum(t.numel() * t.element_size() for t in hphi + hdl + hdz)
+
+        def e2e_step():
+            for d, h in zip(X + G, hX + hG):
+                d.copy_(h, non_blocking=True)
+            step()
+            for h, d in zip(hphi + hdl + hdz, phi + dl + dz):
+                h.copy_(d, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+        for a, b in ee:
+            a.record(stream)
+            e2e_step()
+            b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = float(np.mean([a.elapsed_time(b) for a, b in ee]))
+
+        # accuracy on a sample of rows against the FP64 oracle (outside timing)
+        acc = accuracy_check(works, phi, dl)
+        cpu = cpu_baseline(works, budget_s=args.cpu_seconds)
+        pk = peaks()
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        max_mhz = float(pk.get("sm_max_mhz", 2070.0))
+        peak = fp32_peak_tops(sms, max_mhz)
+        achieved = alg_ops / (kms / 1e3) / 1e12
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "requests": len(works), "sample_trees_per_step": U,
+                       "paths": int(sum(i["n_paths"] for i in infos)),
+                       "n_quad": N_QUAD, "l2": "flushed between steps (256 MB write)",
+                       "accumulation": "f64 across path chunks", "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "alu", "kernel": "batch_kernel<16> (persistent fused forward + adjoint)",
+                         "achieved": achieved, "peak": peak, "unit": "Tops/s (FP32 pipe lane-ops)",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_basis": f"{sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (max SM clock)",
+                         "algorithmic_ops_per_launch": alg_ops, "kernel_ms": kms,
+                         "kernel_ms_source": kms_src},
+            "plain": {"value": U / (plain_ms / 1e3), "unit": UNIT, "ms_per_step": plain_ms,
+                      "kernels": "per request: forward launches + adjoint launches + epilogue",
+                      "speedup_batched": plain_ms / ms},
+            "e2e": {"value": U / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "accuracy": acc,
+            "cpu_baseline": cpu,
+            "gpu_launches": int(n_kern * args.steps),
+            "clocks": clk,
+            "wall_s_timed": wall,
+        }
+    for e in ens:
+        e.close()
+    return out
+
+
+def accuracy_check(works, phi, dl, rows_per=2, max_paths=400000):
+    """Max per-sample error of phi vs the FP64 oracle on a few rows of every
+    request whose oracle cost is bounded, normalised by max(|f(x)|, max|phi|)."""
+    import oracle
+
+    worst = 0.0
+    checked = 0
+    for w, p in zip(works, phi):
+        if w.ens.n_leaves > max_paths:
+            continue
+        rows = np.unique(np.linspace(0, w.M - 1, min(rows_per, w.M)).astype(int))
+        ref = oracle.shap_exact(w.ens, w.X[rows])
+        got = p[rows].cpu().numpy()
+        scale = np.maximum(np.abs(ref.sum(1)), np.abs(ref[:, :-1]).max(1))
+        worst = max(worst, float((np.abs(got - ref).max(1) / scale).max()))
+        checked += len(rows)
+    return {"max_rel_err_phi": worst, "rows_checked": checked, "tolerance": 1e-5}
+
+
+def cpu_baseline(works, budget_s=20.0, rows=1, trees=2):
+    """The FP64 oracle (forward + adjoint, exact expansion) on a bounded
+    sample: `rows` samples x `trees` trees of every request.  The per
+    sample*tree cost of each request is projected to its full M * trees, and the
+    value is the whole batch's sample*trees over the projected CPU time."""
+    import oracle
+
+    cores = oracle.threads()
+    t_total = 0.0
+    proj = 0.0
+    used = 0
+    start = time.time()
+    for w in works:
+        if time.time() - start > budget_s:
+            break
+        sub = w.ens.subset(range(min(trees, w.ens.n_trees)))
+        X = w.X[:rows]
+        G = w.grad_phi[:rows]
+        t0 = time.time()
+        oracle.shap_exact(sub, X, n_threads=cores)
+        oracle.grad_exact(sub, X, G, n_threads=cores)
+        dt = time.time() - t0
+        t_total += dt
+        u = X.shape[0] * sub.n_trees
+        proj += dt / u * (w.M * w.ens.n_trees)
+        used += 1
+    covered = sum(w.M * w.ens.n_trees for w in works[:used])
+    value = covered / proj if proj > 0 else None
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{rows} sample x {trees} trees of each of the first {used} requests "
+                      f"(forward + adjoint, exact FP64 expansion), projected to their full M x trees; "
+                      f"{t_total:.1f}s of CPU work"}
+
+
+# ------------------------------------------------------------ reference arm
+
+def run_reference(args, rank, world):
+    """The FP64 oracle as it stands, on the host cores, same metric/unit."""
+    if rank != 0:
+        return None
+    import oracle
+    import synth
+
+    seed = synth.SEED_BASE + 4
+    trees, depth, feats, samples = synth.batch_draw(seed, 64)
+    sample_trees, rows = 2, 1
+    parts = []
+    for e in range(64):
+        es = seed * 1000 + e
+        n_train = int(min(100000, 20 * 2 ** int(depth[e])))
+        nt = int(min(sample_trees, trees[e]))
+        ens = synth.grow(es, nt, int(depth[e]), int(feats[e]), n_train, 0.1, min_rows=5)
+        X = synth.normal(es, synth.STREAM_X, (int(samples[e]), int(feats[e])))[:rows]
+        G = synth.normal(es, synth.STREAM_GRAD, (int(samples[e]), int(feats[e]) + 1))[:rows]
+        parts.append((ens, X, G, int(samples[e]) * int(trees[e]), nt * rows))
+    cores = oracle.threads()
+
+    def one_step():
+        t = 0.0
+        proj = 0.0
+        for ens, X, G, full, u in parts:
+            t0 = time.time()
+            oracle.shap_exact(ens, X, n_threads=cores)
+            oracle.grad_exact(ens, X, G, n_threads=cores)
+            dt = time.time() - t0
+            t += dt
+            proj += dt / u * full
+        return t, proj
+
+    for _ in range(args.warmup):
+        one_step()
+    ts, projs = [], []
+    for _ in range(args.steps):
+        t, p = one_step()
+        ts.append(t)
+        projs.append(p)
+    full_units = sum(p[3] for p in parts)
+    value = full_units / float(np.mean(projs))
+    sample = (f"{rows} sample x {sample_trees} trees of each of the 64 requests (forward + adjoint, exact FP64 "
+              f"expansion), projected to the full batch's M x trees")
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(np.mean(projs)) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD}, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_seconds_per_step": float(np.mean(ts))},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+
+            torch.distributed.init_process_group("nccl")
+        out = run_ours(args, rank, world, local)
+        if world > 1:
+            import torch
+
+            torch.distributed.destroy_process_group()
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

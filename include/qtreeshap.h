@@ -174,6 +174,13 @@ typedef struct qts_request {
 qts_status qts_batched_fwd_bwd(int32_t n_requests, const qts_request *reqs, int32_t n_quad,
                                qts_stream_t stream);
 
+/* Number of kernels in the graph of the calling thread's last batched call. */
+int32_t qts_batched_kernel_count(void);
+
+/* Device time (ms) of the persistent kernel(s) of the calling thread's last
+ * batched call, from CUDA events recorded inside its graph (waits for them). */
+qts_status qts_batched_last_kernel_ms(float *ms);
+
 /*
  * qts_autotune - time candidate launch configurations (warps per block, paths
  * per chunk, node-group width) for this ensemble and sample count on `stream`,

@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "QTS_OK", 1: "QTS_ERR_ARG", 2: "QTS_ERR_CUDA", 3: "QTS_ERR_OO
 # every symbol include/qtreeshap.h declares
 EXPORTS = ("qts_load_ensemble", "qts_update_params", "qts_shap_values", "qts_shap_interactions",
            "qts_shap_backward", "qts_batched_fwd_bwd", "qts_autotune", "qts_sync_status",
-           "qts_get_info", "qts_describe_ensemble", "qts_gauss_legendre", "qts_last_error",
+           "qts_get_info", "qts_describe_ensemble", "qts_batched_kernel_count", "qts_batched_last_kernel_ms", "qts_gauss_legendre", "qts_last_error",
            "qts_free")
 
 _lib = None
@@ -76,13 +76,16 @@ def lib():
         L.qts_describe_ensemble.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, u32,
                                             ctypes.POINTER(QtsInfo)]
         L.qts_gauss_legendre.argtypes = [i32, vp, vp]
+        L.qts_batched_kernel_count.argtypes = []
+        L.qts_batched_last_kernel_ms.argtypes = [ctypes.POINTER(ctypes.c_float)]
         L.qts_last_error.argtypes = []
         L.qts_last_error.restype = ctypes.c_char_p
         L.qts_free.argtypes = [vp]
         L.qts_free.restype = None
         for f in EXPORTS:
-            if f not in ("qts_last_error", "qts_free"):
+            if f not in ("qts_last_error", "qts_free", "qts_batched_kernel_count"):
                 getattr(L, f).restype = ctypes.c_int
+        L.qts_batched_kernel_count.restype = ctypes.c_int32
         _lib = L
     return _lib
 
@@ -256,6 +259,17 @@ def batched_fwd_bwd(reqs, n_quad: int = 8, stream=None):
     """Run prepared ``make_requests`` in one persistent launch (graph-captured)."""
     _check(lib().qts_batched_fwd_bwd(len(reqs), ctypes.cast(reqs, ctypes.c_void_p), n_quad,
                                      _stream(stream)))
+
+
+def batched_last_kernel_ms() -> float:
+    """Device time of the persistent kernel of this thread's last batched call."""
+    ms = ctypes.c_float()
+    _check(lib().qts_batched_last_kernel_ms(ctypes.byref(ms)))
+    return float(ms.value)
+
+
+def batched_kernel_count() -> int:
+    return int(lib().qts_batched_kernel_count())
 
 
 def autotune(ens: Ensemble, X, cache_path: str | None = None, stream=None):

@@ -40,6 +40,7 @@ static Tune default_tune(int D) {
     t.sub = D <= 16 ? 32 : 16;
     t.paths = D <= 8 ? 512 : (D <= 16 ? 256 : 128);
     t.np = D <= 8 ? 8 : (D <= 24 ? 4 : 2);
+    t.bpaths = 128;
     return t;
 }
 
@@ -97,12 +98,24 @@ qts_status upload(qts_ensemble* e) {
         return st;
     }
     e->device_bytes = tot;
+    // the device copies are the working set; keep only sizes and bucket info
+    Prepared& Pm = e->prep;
+    std::vector<Rec32>().swap(Pm.rec32);
+    std::vector<Rec64>().swap(Pm.rec64);
+    std::vector<int64_t>().swap(Pm.path_leaf);
+    std::vector<double>().swap(Pm.path_zprod);
+    std::vector<double>().swap(Pm.path_val);
+    std::vector<double>().swap(Pm.slot_zexcl);
+    std::vector<int64_t>().swap(Pm.slot_edge_begin);
+    std::vector<int64_t>().swap(Pm.edge_node);
+    std::vector<double>().swap(Pm.edge_coef);
     return QTS_OK;
 }
 
 qts_status ensure_workspace(qts_ensemble* e, size_t bytes) {
     if (bytes <= e->work_bytes) return QTS_OK;
     if (e->d_work) {
+        batch_forget(e);
         cudaError_t err = cudaDeviceSynchronize();
         if (err != cudaSuccess) return cuda_fail(err, "workspace resize sync");
         cudaFree(e->d_work);
@@ -215,6 +228,7 @@ qts_status qts_update_params(qts_ensemble* e, const float* z, const float* leaf_
     }
     cudaError_t ce = cudaDeviceSynchronize();
     if (ce != cudaSuccess) return cuda_fail(ce, "update sync");
+    batch_forget(e);
     release_device(e);
     e->prep = std::move(P);
     return upload(e);
@@ -317,6 +331,7 @@ qts_status qts_describe_ensemble(int32_t n_trees, const int64_t* off, const int3
 
 void qts_free(qts_ensemble* e) {
     if (!e) return;
+    batch_forget(e);
     cudaDeviceSynchronize();
     release_device(e);
     cudaFree(e->d_status);

@@ -1,0 +1,476 @@
+// Batched forward + adjoint of many heterogeneous requests in one persistent
+// kernel, captured (with its initialisation and epilogues) into a CUDA graph.
+//
+// Work items are (request, bucket, path chunk, sample tile of 32).  Items are
+// not materialised: segments (request, bucket) are ordered by per-item cost,
+// heaviest first, and carry their first item index, so a block that takes
+// item k from the atomic counter finds its segment by binary search.  For a
+// request with grad_phi one pass over each (sample, path) yields both phi and
+// the adjoint sums (the forward products P_j S_j are part of the adjoint's).
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+
+#include "qts_paths.cuh"
+
+namespace qts {
+
+struct SegDev {
+    const Rec32* rec;
+    double* g_val;      // bucket-offset adjoint accumulators (nullptr: forward only)
+    double* g_slot;
+    int64_t n_paths;
+    int64_t item_begin;
+    int32_t D;
+    int32_t paths;      // paths per item
+    int32_t n_tiles;
+    int32_t req;
+};
+
+struct ReqDev {
+    const float* X;
+    const float* G;
+    double* phi;
+    int64_t M;
+    int32_t F;
+    int32_t pad;
+    int* status;
+};
+
+struct BatchArgs {
+    const SegDev* segs;
+    int n_segs;
+    const ReqDev* reqs;
+    int64_t n_items;
+    unsigned long long* counter;
+    int Fmax;
+    int sub;
+    QuadF q;
+};
+
+size_t batch_smem_bytes(int Fmax, int sub, int dmax) {
+    size_t off = 3 * (size_t)(Fmax + 1) * kTileLd * 4;
+    off = (off + 15) & ~(size_t)15;
+    off += 2 * (size_t)sub * (dmax + 1) * sizeof(Rec32);
+    off = (off + 15) & ~(size_t)15;
+    return off + 16;
+}
+
+template <int D>
+struct BatchNP {
+    static constexpr int fused = D <= 8 ? 4 : 2;
+    static constexpr int fwd = D <= 8 ? 8 : (D <= 24 ? 4 : 2);
+};
+
+template <int D>
+__device__ __forceinline__ bool batch_item(const SegDev& sg, const ReqDev& rq, int64_t p0, int64_t p1,
+                                           int64_t s0, float* xs, float* gs, float* ps, Rec32* st0,
+                                           Rec32* st1, uint64_t* bars, uint32_t* s_phase, int* s_flag,
+                                           int sub, const QuadF& q) {
+    const int F = rq.F;
+    const int lane = threadIdx.x & 31;
+    for (int idx = threadIdx.x; idx < (F + 1) * kTileLd; idx += blockDim.x) ps[idx] = 0.f;
+    const bool has_nan = load_tile_t(xs, rq.X, s0, rq.M, F, F, 1);
+    const bool grad = rq.G != nullptr;
+    if (grad) load_tile_t(gs, rq.G, s0, rq.M, F, F + 1, 1);
+    const bool ok = stream_paths<Rec32, D>(
+        sg.rec, p0, p1, sub, st0, st1, bars, s_phase, s_flag, rq.status, [&](int64_t p, const Rec32* r) {
+            if (grad) {
+                double* gsl = sg.g_slot + p * D;
+                double* gv = sg.g_val + p;
+                if (has_nan) bwd_path_f32<D, BatchNP<D>::fused, true, true>(r, xs, gs, ps, lane, q, gsl, gv);
+                else bwd_path_f32<D, BatchNP<D>::fused, false, true>(r, xs, gs, ps, lane, q, gsl, gv);
+            } else {
+                if (has_nan) fwd_path_f32<D, BatchNP<D>::fwd, true>(r, xs, ps, lane, q);
+                else fwd_path_f32<D, BatchNP<D>::fwd, false>(r, xs, ps, lane, q);
+            }
+        });
+    if (!ok) return false;
+    if (rq.phi) {
+        for (int idx = threadIdx.x; idx < 32 * F; idx += blockDim.x) {
+            const int s = idx / F, f = idx - s * F;
+            if (s0 + s < rq.M) {
+                const float v = ps[f * kTileLd + s];
+                if (v != 0.f) atomicAdd(&rq.phi[(s0 + s) * (F + 1) + f], (double)v);
+            }
+        }
+    }
+    __syncthreads();  // the tiles are rewritten by the next item
+    return true;
+}
+
+// DCLASS: 16 handles widths 1..16, 32 handles 20..32, 64 handles 40..64.
+template <int DCLASS>
+__global__ void __launch_bounds__(128) batch_kernel(BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const size_t rows = a.Fmax + 1;
+    float* xs = (float*)smem;
+    float* gs = xs + rows * kTileLd;
+    float* ps = gs + rows * kTileLd;
+    size_t off = (3 * rows * kTileLd * 4 + 15) & ~(size_t)15;
+    Rec32* st0 = (Rec32*)(smem + off);
+    Rec32* st1 = st0 + (size_t)a.sub * (DCLASS + 1);
+    uint64_t* bars = (uint64_t*)(st1 + (size_t)a.sub * (DCLASS + 1));
+    __shared__ int s_flag;
+    __shared__ uint32_t s_phase[2];
+    __shared__ long long s_item;
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+        s_phase[0] = s_phase[1] = 0;
+    }
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(a.counter, 1ull);
+        __syncthreads();
+        const int64_t item = s_item;
+        __syncthreads();
+        if (item >= a.n_items) break;
+        int lo = 0, hi = a.n_segs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.segs[mid].item_begin <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const SegDev sg = a.segs[lo];
+        const ReqDev rq = a.reqs[sg.req];
+        const int64_t local = item - sg.item_begin;
+        const int64_t s0 = (local % sg.n_tiles) * 32;
+        const int64_t p0 = (local / sg.n_tiles) * sg.paths;
+        const int64_t p1 = imin64(p0 + sg.paths, sg.n_paths);
+        bool ok = true;
+        switch (sg.D) {
+#define QTS_CASE(DD) \
+    case DD: ok = batch_item<DD>(sg, rq, p0, p1, s0, xs, gs, ps, st0, st1, bars, s_phase, &s_flag, a.sub, a.q); break;
+            default: break;
+            QTS_CASE(DCLASS)
+            QTS_CASE((DCLASS == 16 ? 1 : DCLASS == 32 ? 20 : 40))
+            QTS_CASE((DCLASS == 16 ? 2 : DCLASS == 32 ? 24 : 48))
+            QTS_CASE((DCLASS == 16 ? 3 : DCLASS == 32 ? 28 : 56))
+#undef QTS_CASE
+        }
+        if constexpr (DCLASS == 16) {
+            switch (sg.D) {
+#define QTS_CASE(DD) \
+    case DD: ok = batch_item<DD>(sg, rq, p0, p1, s0, xs, gs, ps, st0, st1, bars, s_phase, &s_flag, a.sub, a.q); break;
+                QTS_CASE(4) QTS_CASE(5) QTS_CASE(6) QTS_CASE(7) QTS_CASE(8) QTS_CASE(9) QTS_CASE(10)
+                QTS_CASE(11) QTS_CASE(12) QTS_CASE(13) QTS_CASE(14) QTS_CASE(15)
+#undef QTS_CASE
+                default: break;
+            }
+        }
+        if (!ok) break;  // a bounded wait ran out: status is set, stop this block
+    }
+}
+
+// ------------------------------------------------------------- host side --
+
+struct BatchPlan {
+    std::vector<uint64_t> key;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    void* dev = nullptr;  // segments, requests, counters
+    int kernels = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the persistent kernel(s)
+};
+
+static std::mutex g_plan_mu;
+static std::vector<BatchPlan*> g_plans;  // most recent last
+static thread_local BatchPlan* g_last_plan = nullptr;
+constexpr size_t kMaxPlans = 8;
+
+static void destroy_plan(BatchPlan* p) {
+    if (p->ev0) cudaEventDestroy(p->ev0);
+    if (p->ev1) cudaEventDestroy(p->ev1);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->dev) cudaFree(p->dev);
+    delete p;
+}
+
+// drop every cached plan that mentions this ensemble (called before it is freed
+// or its device memory moves)
+void batch_forget(const qts_ensemble* e) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    const uint64_t id = (uint64_t)(uintptr_t)e;
+    for (size_t i = 0; i < g_plans.size();) {
+        const auto& k = g_plans[i]->key;
+        if (std::find(k.begin(), k.end(), id) != k.end()) {
+            cudaDeviceSynchronize();
+            if (g_last_plan == g_plans[i]) g_last_plan = nullptr;
+            destroy_plan(g_plans[i]);
+            g_plans.erase(g_plans.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+
+int batch_class(int D) { return D <= 16 ? 16 : (D <= 32 ? 32 : 64); }
+
+template <int C>
+static cudaError_t launch_batch_class(const BatchArgs& a, size_t smem, cudaStream_t st, int* blocks_out) {
+    auto k = batch_kernel<C>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, smem);
+    if (e != cudaSuccess) return e;
+    const int blocks = std::max(1, per_sm) * num_sms();
+    *blocks_out = blocks;
+    k<<<blocks, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// paths per work item: about 2^21 FP32 operations per item
+static int item_paths(int D, bool grad) {
+    const int per_path = 32 * 8 * D * (grad ? 12 : 4);
+    int p = (1 << 21) / std::max(per_path, 1);
+    p = std::max(16, std::min(1024, p));
+    return (p + 15) / 16 * 16;
+}
+
+cudaError_t launch_bwd_epilogue(const qts_ensemble* e, const float* grad, int64_t M, int F,
+                                const double* g_val, const double* g_slot, double* d_leaf,
+                                double* d_z, double* gb, cudaStream_t st);
+
+static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, BatchPlan* plan,
+                             cudaStream_t cap) {
+    struct SegHost {
+        SegDev d;
+        double cost;  // per item
+        int cls;
+    };
+    std::vector<SegHost> segs;
+    std::vector<ReqDev> rd(n);
+    int Fmax = 1;
+    for (int r = 0; r < n; ++r) {
+        const qts_request& R = reqs[r];
+        qts_ensemble* e = R.ens;
+        rd[r] = {R.X, R.grad_phi, R.phi, R.M, R.F, 0, e->d_status};
+        Fmax = std::max(Fmax, R.F);
+        if (R.M <= 0) continue;
+        const bool grad = R.grad_phi != nullptr;
+        double* g_val = grad ? (double*)e->d_work + 4 : nullptr;
+        double* g_slot = grad ? g_val + e->prep.n_paths : nullptr;
+        const int n_tiles = (int)((R.M + 31) / 32);
+        for (const Bucket& b : e->prep.buckets) {
+            SegHost s;
+            s.d.rec = (const Rec32*)e->d_rec + b.rec_off;
+            s.d.g_val = grad ? g_val + b.path_base : nullptr;
+            s.d.g_slot = grad ? g_slot + b.slot_base : nullptr;
+            s.d.n_paths = b.n_paths;
+            s.d.D = b.D;
+            s.d.paths = e->tuned ? e->tune[b.D].bpaths : item_paths(b.D, grad);
+            s.d.n_tiles = n_tiles;
+            s.d.req = r;
+            s.cost = (double)s.d.paths * b.D * (grad ? 12 : 4);
+            s.cls = batch_class(b.D);
+            segs.push_back(s);
+        }
+    }
+    // group by kernel class, heaviest items first within a class
+    std::stable_sort(segs.begin(), segs.end(), [](const SegHost& a, const SegHost& b) {
+        if (a.cls != b.cls) return a.cls < b.cls;
+        return a.cost > b.cost;
+    });
+    const int sub = 16;
+    std::vector<int> cls_list;
+    std::vector<int64_t> cls_items, cls_first_seg;
+    int64_t item = 0;
+    for (size_t i = 0; i < segs.size(); ++i) {
+        if (cls_list.empty() || cls_list.back() != segs[i].cls) {
+            cls_list.push_back(segs[i].cls);
+            cls_first_seg.push_back((int64_t)i);
+            cls_items.push_back(0);
+            item = 0;
+        }
+        segs[i].d.item_begin = item;
+        const int64_t chunks = (segs[i].d.n_paths + segs[i].d.paths - 1) / segs[i].d.paths;
+        item += chunks * segs[i].d.n_tiles;
+        cls_items.back() = item;
+    }
+    const size_t seg_bytes = (sizeof(SegDev) * std::max<size_t>(segs.size(), 1) + 255) / 256 * 256;
+    const size_t req_bytes = (sizeof(ReqDev) * std::max(n, 1) + 255) / 256 * 256;
+    const size_t cnt_bytes = 256;
+    cudaError_t ce = cudaMalloc(&plan->dev, seg_bytes + req_bytes + cnt_bytes);
+    if (ce != cudaSuccess) return cuda_fail(ce, "batch plan allocation");
+    SegDev* d_segs = (SegDev*)plan->dev;
+    ReqDev* d_reqs = (ReqDev*)((char*)plan->dev + seg_bytes);
+    unsigned long long* d_cnt = (unsigned long long*)((char*)plan->dev + seg_bytes + req_bytes);
+    std::vector<SegDev> sd(segs.size());
+    for (size_t i = 0; i < segs.size(); ++i) sd[i] = segs[i].d;
+    if (!sd.empty()) ce = cudaMemcpy(d_segs, sd.data(), sizeof(SegDev) * sd.size(), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(d_reqs, rd.data(), sizeof(ReqDev) * n, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) return cuda_fail(ce, "batch plan upload");
+
+    ce = cudaEventCreate(&plan->ev0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&plan->ev1);
+    if (ce != cudaSuccess) return cuda_fail(ce, "batch plan events");
+    // capture: init, persistent kernel(s), epilogues
+    ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) return cuda_fail(ce, "graph capture begin");
+    int kernels = 0;
+    cudaError_t err = cudaSuccess;
+    for (int r = 0; r < n && err == cudaSuccess; ++r) {
+        const qts_request& R = reqs[r];
+        if (R.phi && R.M > 0) {
+            err = launch_phi_init(R.phi, R.M, R.F, R.ens->prep.bias, cap);
+            ++kernels;
+        }
+        if (R.grad_phi && err == cudaSuccess) {
+            const size_t bytes = sizeof(double) * (size_t)(4 + R.ens->prep.n_paths + R.ens->prep.n_slots);
+            err = cudaMemsetAsync(R.ens->d_work, 0, bytes, cap);
+        }
+    }
+    if (err == cudaSuccess) err = cudaMemsetAsync(d_cnt, 0, cnt_bytes, cap);
+    if (err == cudaSuccess) err = cudaEventRecordWithFlags(plan->ev0, cap, cudaEventRecordExternal);
+    for (size_t c = 0; c < cls_list.size() && err == cudaSuccess; ++c) {
+        const int cls = cls_list[c];
+        BatchArgs a;
+        a.segs = d_segs + cls_first_seg[c];
+        a.n_segs = (int)((c + 1 < cls_list.size() ? cls_first_seg[c + 1] : (int64_t)segs.size()) - cls_first_seg[c]);
+        a.reqs = d_reqs;
+        a.n_items = cls_items[c];
+        a.counter = d_cnt + c;
+        a.Fmax = Fmax;
+        a.sub = sub;
+        a.q = q;
+        const size_t smem = batch_smem_bytes(Fmax, sub, cls);
+        int blocks = 0;
+        if (cls == 16) err = launch_batch_class<16>(a, smem, cap, &blocks);
+        else if (cls == 32) err = launch_batch_class<32>(a, smem, cap, &blocks);
+        else err = launch_batch_class<64>(a, smem, cap, &blocks);
+        ++kernels;
+    }
+    if (err == cudaSuccess) err = cudaEventRecordWithFlags(plan->ev1, cap, cudaEventRecordExternal);
+    for (int r = 0; r < n && err == cudaSuccess; ++r) {
+        const qts_request& R = reqs[r];
+        if (!R.grad_phi) continue;
+        double* gb = (double*)R.ens->d_work;
+        double* g_val = gb + 4;
+        double* g_slot = g_val + R.ens->prep.n_paths;
+        if (R.M > 0) {
+            err = launch_bwd_epilogue(R.ens, R.grad_phi, R.M, R.F, g_val, g_slot, R.d_leaf, R.d_z, gb, cap);
+            kernels += 1 + (R.ens->prep.n_paths + (int64_t)R.ens->prep.empty_leaf.size() > 0) +
+                       (R.ens->prep.n_slots > 0);
+        } else {
+            err = cudaMemsetAsync(R.d_leaf, 0, sizeof(double) * R.ens->n_nodes, cap);
+            if (err == cudaSuccess) err = cudaMemsetAsync(R.d_z, 0, sizeof(double) * R.ens->n_nodes, cap);
+        }
+    }
+    cudaGraph_t g = nullptr;
+    ce = cudaStreamEndCapture(cap, &g);
+    if (err != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(err, "batched launch during capture");
+    }
+    if (ce != cudaSuccess) return cuda_fail(ce, "graph capture end");
+    plan->graph = g;
+    ce = cudaGraphInstantiate(&plan->exec, g, 0);
+    if (ce != cudaSuccess) return cuda_fail(ce, "graph instantiate");
+    plan->kernels = kernels;
+    return QTS_OK;
+}
+
+static thread_local int g_last_batch_kernels = 0;
+
+}  // namespace qts
+
+using namespace qts;
+
+extern "C" qts_status qts_batched_fwd_bwd(int32_t n, const qts_request* reqs, int32_t n_quad,
+                                          qts_stream_t stream) {
+    if (n < 1 || !reqs) return fail(QTS_ERR_ARG, "no requests");
+    QuadF qf;
+    if (!make_quad(n_quad, &qf, nullptr)) return fail(QTS_ERR_ARG, "n_quad must be in [1, 32]");
+    for (int r = 0; r < n; ++r) {
+        const qts_request& R = reqs[r];
+        qts_status st = check_call(R.ens, R.X, R.M, R.F, n_quad);
+        if (st != QTS_OK) return fail(st, "request " + std::to_string(r) + ": " + qts_last_error());
+        if (R.ens->flags & QTS_FLAG_FP64)
+            return fail(QTS_ERR_UNSUPPORTED, "request " + std::to_string(r) + ": batched calls use FP32 tables");
+        if (!R.grad_phi && !R.phi) return fail(QTS_ERR_ARG, "request " + std::to_string(r) + ": nothing to compute");
+        if (R.grad_phi && (!R.d_leaf || !R.d_z))
+            return fail(QTS_ERR_ARG, "request " + std::to_string(r) + ": d_leaf/d_z are NULL");
+        for (int s = 0; s < r; ++s)
+            if (reqs[s].ens == R.ens)
+                return fail(QTS_ERR_ARG, "an ensemble may appear in at most one request of a batch");
+    }
+    for (int r = 0; r < n; ++r) {
+        const qts_request& R = reqs[r];
+        if (!R.grad_phi) continue;
+        void* before = R.ens->d_work;
+        qts_status st = ensure_workspace(
+            R.ens, sizeof(double) * (size_t)(4 + R.ens->prep.n_paths + R.ens->prep.n_slots));
+        if (st != QTS_OK) return st;
+        if (before && before != R.ens->d_work) batch_forget(R.ens);
+    }
+    std::vector<uint64_t> key;
+    key.push_back((uint64_t)n_quad);
+    for (int r = 0; r < n; ++r) {
+        const qts_request& R = reqs[r];
+        for (uint64_t v : {(uint64_t)(uintptr_t)R.ens, (uint64_t)(uintptr_t)R.X, (uint64_t)R.M, (uint64_t)R.F,
+                           (uint64_t)(uintptr_t)R.grad_phi, (uint64_t)(uintptr_t)R.phi,
+                           (uint64_t)(uintptr_t)R.d_leaf, (uint64_t)(uintptr_t)R.d_z,
+                           (uint64_t)(uintptr_t)R.ens->d_work, (uint64_t)(uintptr_t)R.ens->d_rec,
+                           (uint64_t)R.ens->tuned})
+            key.push_back(v);
+    }
+    cudaGraphExec_t exec = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        for (size_t i = 0; i < g_plans.size(); ++i) {
+            if (g_plans[i]->key == key) {
+                BatchPlan* p = g_plans[i];
+                g_plans.erase(g_plans.begin() + i);
+                g_plans.push_back(p);
+                exec = p->exec;
+                g_last_batch_kernels = p->kernels;
+                g_last_plan = p;
+                break;
+            }
+        }
+    }
+    if (!exec) {
+        cudaStream_t cap;
+        cudaError_t ce = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (ce != cudaSuccess) return cuda_fail(ce, "capture stream");
+        auto* plan = new BatchPlan();
+        plan->key = key;
+        qts_status st = build_plan(n, reqs, qf, plan, cap);
+        cudaStreamDestroy(cap);
+        if (st != QTS_OK) {
+            destroy_plan(plan);
+            return st;
+        }
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        if (g_plans.size() >= kMaxPlans) {
+            cudaDeviceSynchronize();
+            if (g_last_plan == g_plans.front()) g_last_plan = nullptr;
+            destroy_plan(g_plans.front());
+            g_plans.erase(g_plans.begin());
+        }
+        g_plans.push_back(plan);
+        exec = plan->exec;
+        g_last_batch_kernels = plan->kernels;
+        g_last_plan = plan;
+    }
+    cudaError_t ce = cudaGraphLaunch(exec, (cudaStream_t)stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "graph launch");
+    return QTS_OK;
+}
+
+extern "C" int32_t qts_batched_kernel_count(void) { return g_last_batch_kernels; }
+
+extern "C" qts_status qts_batched_last_kernel_ms(float* ms) {
+    if (!ms) return fail(QTS_ERR_ARG, "ms is NULL");
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    if (!g_last_plan || std::find(g_plans.begin(), g_plans.end(), g_last_plan) == g_plans.end())
+        return fail(QTS_ERR_ARG, "no batched call on this thread");
+    cudaError_t ce = cudaEventSynchronize(g_last_plan->ev1);
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(ms, g_last_plan->ev0, g_last_plan->ev1);
+    return ce == cudaSuccess ? QTS_OK : cuda_fail(ce, "batched kernel timing");
+}

@@ -13,7 +13,7 @@
 #include <algorithm>
 #include <type_traits>
 
-#include "qts_device.cuh"
+#include "qts_paths.cuh"
 
 namespace qts {
 
@@ -31,104 +31,6 @@ struct FwdArgs {
     QuadF q;
     QuadD qd;
 };
-
-// ------------------------------------------------------------------ FP32 --
-
-template <int D, int NP, bool HAS_NAN>
-__device__ __forceinline__ void fwd_path_f32(const Rec32* __restrict__ r, const float* __restrict__ xs,
-                                             float* ps, int lane, const QuadF& q) {
-    constexpr int K = NP / 2;  // node pairs per pass
-    const float val = r[0].z;
-    float dd[D], zz[D];
-    int ff[D];
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-        const Rec32 e = r[1 + j];
-        const int f = feat_of(e.bits);
-        const float x = xs[f * kTileLd + lane];
-        const bool o = satisfies<HAS_NAN>(x, e.lo, e.hi, e.bits);
-        dd[j] = (o ? 1.f : 0.f) - e.z;
-        zz[j] = e.z;
-        ff[j] = f;
-    }
-    float cacc[D];
-#pragma unroll
-    for (int j = 0; j < D; ++j) cacc[j] = 0.f;
-    const int npass = q.n_pad / NP;
-    for (int pass = 0; pass < npass; ++pass) {
-        float2 T[K], P[D][K], A[D][K], S[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const int m = pass * NP + 2 * k;
-            T[k] = f2(q.t[m], q.t[m + 1]);
-            P[0][k] = f2(q.w[m] * val, q.w[m + 1] * val);
-        }
-        // prefix products P_j = w val prod_{l<j} a_l
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                A[j][k] = fma2(T[k], f2s(dd[j]), f2s(zz[j]));
-                if (j + 1 < D) P[j + 1][k] = mul2(P[j][k], A[j][k]);
-            }
-        }
-        // suffix products, combined on the way down
-#pragma unroll
-        for (int k = 0; k < K; ++k) S[k] = f2s(1.f);
-#pragma unroll
-        for (int j = D - 1; j >= 0; --j) {
-            float2 acc = mul2(P[j][0], S[0]);
-#pragma unroll
-            for (int k = 1; k < K; ++k) acc = fma2(P[j][k], S[k], acc);
-            if (j > 0) {
-#pragma unroll
-                for (int k = 0; k < K; ++k) S[k] = mul2(S[k], A[j][k]);
-            }
-            cacc[j] += acc.x + acc.y;
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < D; ++j) atomicAdd(&ps[ff[j] * kTileLd + lane], dd[j] * cacc[j]);
-}
-
-// ------------------------------------------------------------------ FP64 --
-
-template <int D, bool HAS_NAN>
-__device__ __forceinline__ void fwd_path_f64(const Rec64* __restrict__ r, const float* __restrict__ xs,
-                                             double* ps, int lane, const QuadD& q) {
-    const double val = r[0].z;
-    double dd[D], zz[D], cacc[D];
-    int ff[D];
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-        const Rec64 e = r[1 + j];
-        const int f = feat_of(e.bits);
-        const float x = xs[f * kTileLd + lane];
-        const bool o = satisfies<HAS_NAN>(x, e.lo, e.hi, e.bits);
-        dd[j] = (o ? 1.0 : 0.0) - e.z;
-        zz[j] = e.z;
-        ff[j] = f;
-        cacc[j] = 0.0;
-    }
-    for (int m = 0; m < q.n; ++m) {
-        const double t = q.t[m];
-        double A[D], P[D];
-        P[0] = q.w[m] * val;
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-            A[j] = fma(t, dd[j], zz[j]);
-            if (j + 1 < D) P[j + 1] = P[j] * A[j];
-        }
-        double S = 1.0;
-#pragma unroll
-        for (int j = D - 1; j >= 0; --j) {
-            cacc[j] += P[j] * S;
-            S *= A[j];
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < D; ++j) atomicAdd(&ps[ff[j] * kTileLd + lane], dd[j] * cacc[j]);
-}
 
 // --------------------------------------------------------------- kernel ---
 

@@ -84,6 +84,7 @@ struct Tune {
     int paths = 128;      // paths per block (chunk)
     int sub = 32;         // paths per staged sub-chunk
     int np = 8;           // nodes per register pass (8, 4 or 2)
+    int bpaths = 128;     // paths per work item of the fused forward + adjoint pass
 };
 
 }  // namespace qts
@@ -130,6 +131,7 @@ qts_status ensure_workspace(qts_ensemble* e, size_t bytes);
 qts_status upload(qts_ensemble* e);
 void release_device(qts_ensemble* e);
 int num_sms();
+void batch_forget(const qts_ensemble* e);  // drop cached batched graphs using e
 
 // GL nodes packed for the kernels (fp32 and fp64), padded to a multiple of 8
 // with zero-weight nodes at t = 1/2.

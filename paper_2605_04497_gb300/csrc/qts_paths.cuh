@@ -1,0 +1,307 @@
+// Per-path device routines shared by the per-bucket kernels and the batched
+// persistent kernel.  Lane = sample; all path records are warp-uniform.
+#pragma once
+
+#include <type_traits>
+
+#include "qts_device.cuh"
+
+namespace qts {
+
+// ====================================================== first order ======
+//
+// c_i = sum_m w_m val prod_{j<i} a_j(t_m) prod_{j>i} a_j(t_m), a_j(t) = z_j + t (o_j - z_j),
+// by a prefix product seeded with w_m val and a suffix product (no division),
+// two quadrature nodes per f32x2 register pair; phi[f_i] += (o_i - z_i) c_i
+// (Thm 1 with S = {i}, Eq. shap_as_weighted_banzhafs).
+
+
+template <int D, int NP, bool HAS_NAN>
+__device__ __forceinline__ void fwd_path_f32(const Rec32* __restrict__ r, const float* __restrict__ xs,
+                                             float* ps, int lane, const QuadF& q) {
+    constexpr int K = NP / 2;  // node pairs per pass
+    const float val = r[0].z;
+    float dd[D], zz[D];
+    int ff[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const Rec32 e = r[1 + j];
+        const int f = feat_of(e.bits);
+        const float x = xs[f * kTileLd + lane];
+        const bool o = satisfies<HAS_NAN>(x, e.lo, e.hi, e.bits);
+        dd[j] = (o ? 1.f : 0.f) - e.z;
+        zz[j] = e.z;
+        ff[j] = f;
+    }
+    float cacc[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) cacc[j] = 0.f;
+    const int npass = q.n_pad / NP;
+    for (int pass = 0; pass < npass; ++pass) {
+        float2 T[K], P[D][K], A[D][K], S[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int m = pass * NP + 2 * k;
+            T[k] = f2(q.t[m], q.t[m + 1]);
+            P[0][k] = f2(q.w[m] * val, q.w[m + 1] * val);
+        }
+        // prefix products P_j = w val prod_{l<j} a_l
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                A[j][k] = fma2(T[k], f2s(dd[j]), f2s(zz[j]));
+                if (j + 1 < D) P[j + 1][k] = mul2(P[j][k], A[j][k]);
+            }
+        }
+        // suffix products, combined on the way down
+#pragma unroll
+        for (int k = 0; k < K; ++k) S[k] = f2s(1.f);
+#pragma unroll
+        for (int j = D - 1; j >= 0; --j) {
+            float2 acc = mul2(P[j][0], S[0]);
+#pragma unroll
+            for (int k = 1; k < K; ++k) acc = fma2(P[j][k], S[k], acc);
+            if (j > 0) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) S[k] = mul2(S[k], A[j][k]);
+            }
+            cacc[j] += acc.x + acc.y;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) atomicAdd(&ps[ff[j] * kTileLd + lane], dd[j] * cacc[j]);
+}
+
+
+template <int D, bool HAS_NAN>
+__device__ __forceinline__ void fwd_path_f64(const Rec64* __restrict__ r, const float* __restrict__ xs,
+                                             double* ps, int lane, const QuadD& q) {
+    const double val = r[0].z;
+    double dd[D], zz[D], cacc[D];
+    int ff[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const Rec64 e = r[1 + j];
+        const int f = feat_of(e.bits);
+        const float x = xs[f * kTileLd + lane];
+        const bool o = satisfies<HAS_NAN>(x, e.lo, e.hi, e.bits);
+        dd[j] = (o ? 1.0 : 0.0) - e.z;
+        zz[j] = e.z;
+        ff[j] = f;
+        cacc[j] = 0.0;
+    }
+    for (int m = 0; m < q.n; ++m) {
+        const double t = q.t[m];
+        double A[D], P[D];
+        P[0] = q.w[m] * val;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            A[j] = fma(t, dd[j], zz[j]);
+            if (j + 1 < D) P[j + 1] = P[j] * A[j];
+        }
+        double S = 1.0;
+#pragma unroll
+        for (int j = D - 1; j >= 0; --j) {
+            cacc[j] += P[j] * S;
+            S *= A[j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) atomicAdd(&ps[ff[j] * kTileLd + lane], dd[j] * cacc[j]);
+}
+
+
+// =========================================================== adjoint =====
+
+// ------------------------------------------------- warp transpose-reduce --
+//
+// Each lane holds N values (N a power of two <= 32).  log2(N) halving steps
+// exchange half of the values with the partner lane at distance 16, 8, ...,
+// keeping the other half, so that after them lane L holds, summed over a group
+// of lanes, the value with index L >> (5 - log2 N); the remaining distances
+// finish the sum.  N - 1 + (5 - log2 N) shuffles instead of 5 N.
+template <int N>
+__device__ __forceinline__ float transpose_reduce(float (&v)[N], int lane) {
+    static_assert(N >= 1 && N <= 32 && (N & (N - 1)) == 0, "N must be a power of two <= 32");
+#pragma unroll
+    for (int half = N / 2, off = 16; half >= 1; half >>= 1, off >>= 1) {
+        const bool upper = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float send = upper ? v[i] : v[i + half];
+            const float keep = upper ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    float r = v[0];
+    constexpr int LOG = (N >= 32) ? 5 : (N >= 16) ? 4 : (N >= 8) ? 3 : (N >= 4) ? 2 : (N >= 2) ? 1 : 0;
+#pragma unroll
+    for (int off = (16 >> LOG); off >= 1; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+    return r;
+}
+
+constexpr int pow2_at_least(int x) { return x <= 1 ? 1 : 2 * pow2_at_least((x + 1) / 2); }
+
+// Reduce dz[0..D) and dval over the warp and add them to the FP64 accumulators.
+template <int D, typename T>
+__device__ __forceinline__ void flush_path_grads(T (&dz)[D], T dval, int lane, double* g_slot_p,
+                                                 double* g_val_p) {
+    if constexpr (std::is_same<T, float>::value && D + 1 <= 32) {
+        constexpr int N = pow2_at_least(D + 1);
+        constexpr int LOG = (N >= 32) ? 5 : (N >= 16) ? 4 : (N >= 8) ? 3 : (N >= 4) ? 2 : (N >= 2) ? 1 : 0;
+        float v[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] = i < D ? dz[i] : (i == D ? dval : 0.f);
+        const float r = transpose_reduce<N>(v, lane);
+        const int idx = lane >> (5 - LOG);
+        if ((lane & ((1 << (5 - LOG)) - 1)) == 0) {
+            if (idx < D) atomicAdd(&g_slot_p[idx], (double)r);
+            else if (idx == D) atomicAdd(g_val_p, (double)r);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j <= D; ++j) {
+            T x = j < D ? dz[j] : dval;
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            if (lane == 0) {
+                if (j < D) atomicAdd(&g_slot_p[j], (double)x);
+                else atomicAdd(g_val_p, (double)x);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ FP32 --
+
+template <int D, int NP, bool HAS_NAN, bool WITH_PHI>
+__device__ __forceinline__ void bwd_path_f32(const Rec32* __restrict__ r, const float* __restrict__ xs,
+                                             const float* __restrict__ gs, float* ps, int lane,
+                                             const QuadF& q, double* g_slot_p, double* g_val_p) {
+    constexpr int K = NP / 2;
+    const float val = r[0].z;
+    float dd[D], uu[D], acc1[D], acc2[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const Rec32 e = r[1 + j];
+        const int f = feat_of(e.bits);
+        const float x = xs[f * kTileLd + lane];
+        const bool o = satisfies<HAS_NAN>(x, e.lo, e.hi, e.bits);
+        dd[j] = (o ? 1.f : 0.f) - e.z;
+        uu[j] = gs[f * kTileLd + lane] * dd[j];
+        acc1[j] = 0.f;
+        acc2[j] = 0.f;
+    }
+    const int npass = q.n_pad / NP;
+    for (int pass = 0; pass < npass; ++pass) {
+        float2 T[K], C2[K], A[D][K], P[D][K], PU[D][K], S[K], SU[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int m = pass * NP + 2 * k;
+            T[k] = f2(q.t[m], q.t[m + 1]);
+            C2[k] = f2(1.f - q.t[m], 1.f - q.t[m + 1]);
+            P[0][k] = f2(q.w[m], q.w[m + 1]);
+            PU[0][k] = f2s(0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const float2 z2 = f2s(r[1 + j].z), d2 = f2s(dd[j]), u2 = f2s(uu[j]);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                A[j][k] = fma2(T[k], d2, z2);
+                if (j + 1 < D) {
+                    P[j + 1][k] = mul2(P[j][k], A[j][k]);
+                    PU[j + 1][k] = fma2(PU[j][k], A[j][k], mul2(u2, P[j][k]));
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            S[k] = f2s(1.f);
+            SU[k] = f2s(0.f);
+        }
+#pragma unroll
+        for (int j = D - 1; j >= 0; --j) {
+            const float2 u2 = f2s(uu[j]);
+            float2 a1 = mul2(P[j][0], S[0]);
+            float2 a2 = mul2(C2[0], fma2(P[j][0], SU[0], mul2(PU[j][0], S[0])));
+#pragma unroll
+            for (int k = 1; k < K; ++k) {
+                a1 = fma2(P[j][k], S[k], a1);
+                a2 = fma2(C2[k], fma2(P[j][k], SU[k], mul2(PU[j][k], S[k])), a2);
+            }
+            if (j > 0) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    SU[k] = fma2(SU[k], A[j][k], mul2(u2, S[k]));
+                    S[k] = mul2(S[k], A[j][k]);
+                }
+            }
+            acc1[j] += a1.x + a1.y;
+            acc2[j] += a2.x + a2.y;
+        }
+    }
+    float dval = 0.f, dz[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const int f = feat_of(r[1 + j].bits);
+        dval = fmaf(uu[j], acc1[j], dval);
+        dz[j] = val * (acc2[j] - gs[f * kTileLd + lane] * acc1[j]);
+        if constexpr (WITH_PHI) atomicAdd(&ps[f * kTileLd + lane], val * dd[j] * acc1[j]);
+    }
+    flush_path_grads<D, float>(dz, dval, lane, g_slot_p, g_val_p);
+}
+
+// ------------------------------------------------------------------ FP64 --
+
+template <int D, bool HAS_NAN>
+__device__ __forceinline__ void bwd_path_f64(const Rec64* __restrict__ r, const float* __restrict__ xs,
+                                             const float* __restrict__ gs, int lane, const QuadD& q,
+                                             double* g_slot_p, double* g_val_p) {
+    const double val = r[0].z;
+    double dd[D], uu[D], acc1[D], acc2[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const Rec64 e = r[1 + j];
+        const int f = feat_of(e.bits);
+        const float x = xs[f * kTileLd + lane];
+        const bool o = satisfies<HAS_NAN>(x, e.lo, e.hi, e.bits);
+        dd[j] = (o ? 1.0 : 0.0) - e.z;
+        uu[j] = (double)gs[f * kTileLd + lane] * dd[j];
+        acc1[j] = acc2[j] = 0.0;
+    }
+    for (int m = 0; m < q.n; ++m) {
+        const double t = q.t[m];
+        double A[D], P[D], PU[D];
+        P[0] = q.w[m];
+        PU[0] = 0.0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            A[j] = fma(t, dd[j], r[1 + j].z);
+            if (j + 1 < D) {
+                P[j + 1] = P[j] * A[j];
+                PU[j + 1] = fma(PU[j], A[j], uu[j] * P[j]);
+            }
+        }
+        double S = 1.0, SU = 0.0;
+#pragma unroll
+        for (int j = D - 1; j >= 0; --j) {
+            acc1[j] = fma(P[j], S, acc1[j]);
+            acc2[j] = fma(1.0 - t, fma(P[j], SU, PU[j] * S), acc2[j]);
+            SU = fma(SU, A[j], uu[j] * S);
+            S *= A[j];
+        }
+    }
+    double dval = 0.0, dz[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const int f = feat_of(r[1 + j].bits);
+        dval = fma(uu[j], acc1[j], dval);
+        dz[j] = val * (acc2[j] - (double)gs[f * kTileLd + lane] * acc1[j]);
+    }
+    flush_path_grads<D, double>(dz, dval, lane, g_slot_p, g_val_p);
+}
+
+
+}  // namespace qts

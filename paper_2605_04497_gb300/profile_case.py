@@ -1,0 +1,88 @@
+"""Run one kernel case a few times, for profilers (ncu) and quick timing.
+
+    python -m paper_2605_04497_gb300.profile_case <case> [--reps R]
+
+Cases (synthetic inputs from `synth`):
+  forward-xgb        qts_shap_values on the 1,000-tree depth-8 ensemble, M = 10,000
+  adjoint-xgb        qts_shap_backward on the same
+  interactions-500   qts_shap_interactions on the 500-tree depth-6 ensemble, F = 30, M = 2,000
+  fused-xgb          qts_batched_fwd_bwd with the depth-8 ensemble as a single request
+  fused-deep         qts_batched_fwd_bwd, one request shaped like the heaviest member of the
+                     64-ensemble batch (depth 14, F = 57), 60 trees, M = 4,096
+  adjoint-deep       qts_shap_backward on the same
+Prints the median CUDA-event time per call and the algorithmic FP32-pipe
+operation rate (4 ops per sample x element x node forward, 11 adjoint/fused).
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    import torch
+
+    import synth
+    import paper_2605_04497_gb300 as qts
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["forward-xgb", "adjoint-xgb", "interactions-500", "fused-xgb",
+                                     "fused-deep", "adjoint-deep"])
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args()
+    if args.case.endswith("-deep"):
+        seed = synth.SEED_BASE + 4
+        trees, depth, feats, samples = synth.batch_draw(seed, 64)
+        e = int(np.argmax(trees * samples * 2.0 ** np.minimum(depth, 14)))
+        es = seed * 1000 + e
+        F = int(feats[e])
+        ens = synth.grow(es, 60, int(depth[e]), F, int(min(100000, 20 * 2 ** int(depth[e]))), 0.1, min_rows=5)
+        w = synth.Workload("deep", ens, synth.normal(es, synth.STREAM_X, (4096, F)),
+                           synth.normal(es, synth.STREAM_GRAD, (4096, F + 1)))
+    else:
+        cfg = 3 if args.case == "interactions-500" else 1
+        w = synth.single_config(cfg, with_grad=True)
+    E = qts.Ensemble.from_arrays(w.ens)
+    info = E.info()
+    X = torch.from_numpy(w.X).cuda()
+    G = torch.from_numpy(w.grad_phi).cuda()
+    phi = torch.empty((w.M, w.F + 1), dtype=torch.float64, device="cuda")
+    dl = torch.empty(E.n_nodes, dtype=torch.float64, device="cuda")
+    dz = torch.empty(E.n_nodes, dtype=torch.float64, device="cuda")
+    reqs = qts.make_requests([dict(ens=E, X=X, grad_phi=G, phi=phi, d_leaf=dl, d_z=dz)])
+    fn, ops = {
+        "forward-xgb": (lambda: qts.shap_values(E, X, 8, out=phi), 4),
+        "adjoint-xgb": (lambda: qts.shap_backward(E, X, G, 8), 11),
+        "interactions-500": (lambda: qts.shap_interactions(E, X, 8), 0),
+        "fused-xgb": (lambda: qts.batched_fwd_bwd(reqs, 8), 11),
+        "fused-deep": (lambda: qts.batched_fwd_bwd(reqs, 8), 11),
+        "adjoint-deep": (lambda: qts.shap_backward(E, X, G, 8), 11),
+    }[args.case]
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    E.sync_status()
+    ms = float(np.median(ts))
+    work = ops * 8 * info["sum_unique"] * w.M
+    print(f"{args.case}: paths {info['n_paths']}, buckets {info['buckets']}")
+    print(f"{args.case}: {ms:.3f} ms/call, {w.M * w.ens.n_trees / ms * 1e3:.3e} sample*trees/s"
+          + (f", {work / ms / 1e9:.2f} Tops/s algorithmic" if ops else ""))
+    E.close()
+
+
+if __name__ == "__main__":
+    main()
