@@ -24,17 +24,29 @@ struct SegDev {
     int64_t item_begin;
     int32_t D;
     int32_t paths;      // paths per item
-    int32_t n_tiles;
+    int32_t n_tiles;    // sample groups per chunk (a group = 32, or 32 per warp when priv)
     int32_t req;
+    int32_t priv;       // 1: each warp owns 32 samples and a private phi tile
+    int32_t pad;
 };
 
+// Requests with F + 1 <= kPrivRows use per-warp private phi tiles (plain
+// read-add-write); wider ones share one tile with shared-memory atomics.
+constexpr int kPrivRows = 64;
+constexpr int kBatchWarps = 4;
+
+// Per request: x and grad_phi transposed to [feature][Mpad] (row F of XT is
+// zero for padding elements; columns >= M are zero), so a warp reads one
+// feature of its 32 samples as one coalesced 128-byte line.
 struct ReqDev {
-    const float* X;
-    const float* G;
+    const float* XT;
+    const float* GT;    // nullptr: forward only
     double* phi;
     int64_t M;
+    int64_t Mpad;
     int32_t F;
     int32_t pad;
+    const int* has_nan;
     int* status;
 };
 
@@ -44,55 +56,116 @@ struct BatchArgs {
     const ReqDev* reqs;
     int64_t n_items;
     unsigned long long* counter;
-    int Fmax;
+    int tile_rows;      // rows of the phi region (max of shared and private needs)
     int sub;
     QuadF q;
 };
 
-size_t batch_smem_bytes(int Fmax, int sub, int dmax) {
-    size_t off = 3 * (size_t)(Fmax + 1) * kTileLd * 4;
+size_t batch_smem_bytes(int rows, int sub, int dmax) {
+    size_t off = (size_t)rows * kTileLd * 4;
     off = (off + 15) & ~(size_t)15;
     off += 2 * (size_t)sub * (dmax + 1) * sizeof(Rec32);
     off = (off + 15) & ~(size_t)15;
     return off + 16;
 }
 
+// node-group width and register policy per width (fits 3 blocks of 128 threads)
 template <int D>
 struct BatchNP {
-    static constexpr int fused = D <= 8 ? 4 : 2;
-    static constexpr int fwd = D <= 8 ? 8 : (D <= 24 ? 4 : 2);
+    static constexpr bool packed = D <= 16;  // bwd_path_f32_pk
+    static constexpr int fused = 2;          // otherwise: lean per-pass variant
+    static constexpr bool recomp = true;
+    static constexpr int fwd = D <= 8 ? 8 : 2;
 };
+
+// out[c * Mpad + s] = in[s * ld + c] for c < ncols, s < M; zero elsewhere
+// (rows up to nrows, columns up to Mpad).
+__global__ void transpose_pad_kernel(const float* __restrict__ in, int64_t M, int ncols, int64_t ld,
+                                     float* __restrict__ out, int nrows, int64_t Mpad, int* has_nan) {
+    __shared__ float tile[32][33];
+    const int64_t s0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    int nan_seen = 0;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t s = s0 + r;
+        const int c = c0 + threadIdx.x;
+        float v = 0.f;
+        if (s < M && c < ncols) v = in[s * ld + c];
+        nan_seen |= (v != v);
+        tile[r][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int c = c0 + r;
+        const int64_t s = s0 + threadIdx.x;
+        if (c < nrows && s < Mpad) out[(int64_t)c * Mpad + s] = tile[threadIdx.x][r];
+    }
+    if (has_nan && nan_seen) atomicOr(has_nan, 1);
+}
 
 template <int D>
 __device__ __forceinline__ bool batch_item(const SegDev& sg, const ReqDev& rq, int64_t p0, int64_t p1,
-                                           int64_t s0, float* xs, float* gs, float* ps, Rec32* st0,
-                                           Rec32* st1, uint64_t* bars, uint32_t* s_phase, int* s_flag,
-                                           int sub, const QuadF& q) {
+                                           int64_t s0, float* ps, Rec32* st0, Rec32* st1, uint64_t* bars,
+                                           uint32_t* s_phase, int* s_flag, int sub, const QuadF& q) {
     const int F = rq.F;
-    const int lane = threadIdx.x & 31;
-    for (int idx = threadIdx.x; idx < (F + 1) * kTileLd; idx += blockDim.x) ps[idx] = 0.f;
-    const bool has_nan = load_tile_t(xs, rq.X, s0, rq.M, F, F, 1);
-    const bool grad = rq.G != nullptr;
-    if (grad) load_tile_t(gs, rq.G, s0, rq.M, F, F + 1, 1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool priv = sg.priv != 0;
+    const int tile_elems = (F + 1) * kTileLd;
+    // private mode: warp w owns samples s0 + 32 w .. and tile w
+    float* my = priv ? ps + warp * tile_elems : ps;
+    const int64_t sw = priv ? s0 + 32 * warp : s0;
+    if (priv) {
+        for (int idx = lane; idx < tile_elems; idx += 32) my[idx] = 0.f;
+    } else {
+        for (int idx = threadIdx.x; idx < tile_elems; idx += blockDim.x) ps[idx] = 0.f;
+    }
+    __syncthreads();
+    const bool has_nan = *rq.has_nan != 0;
+    const bool grad = rq.GT != nullptr;
+    const GlobalCols xr{rq.XT, rq.Mpad, sw + lane};
+    const GlobalCols gr{rq.GT, rq.Mpad, sw + lane};
+    constexpr int FWD_NP = BatchNP<D>::fwd;
     const bool ok = stream_paths<Rec32, D>(
-        sg.rec, p0, p1, sub, st0, st1, bars, s_phase, s_flag, rq.status, [&](int64_t p, const Rec32* r) {
+        sg.rec, p0, p1, sub, st0, st1, bars, s_phase, s_flag, rq.status,
+        [&](int64_t p, const Rec32* r) {
             if (grad) {
                 double* gsl = sg.g_slot + p * D;
                 double* gv = sg.g_val + p;
-                if (has_nan) bwd_path_f32<D, BatchNP<D>::fused, true, true>(r, xs, gs, ps, lane, q, gsl, gv);
-                else bwd_path_f32<D, BatchNP<D>::fused, false, true>(r, xs, gs, ps, lane, q, gsl, gv);
+                if (priv) {
+                    if (has_nan) bwd_path_f32_pk<D, true, kPhiPrivate>(r, xr, gr, my, lane, q, gsl, gv);
+                    else bwd_path_f32_pk<D, false, kPhiPrivate>(r, xr, gr, my, lane, q, gsl, gv);
+                } else {
+                    if (has_nan) bwd_path_f32_pk<D, true, kPhiAtomic>(r, xr, gr, my, lane, q, gsl, gv);
+                    else bwd_path_f32_pk<D, false, kPhiAtomic>(r, xr, gr, my, lane, q, gsl, gv);
+                }
             } else {
-                if (has_nan) fwd_path_f32<D, BatchNP<D>::fwd, true>(r, xs, ps, lane, q);
-                else fwd_path_f32<D, BatchNP<D>::fwd, false>(r, xs, ps, lane, q);
+                if (priv) {
+                    if (has_nan) fwd_path_f32<D, FWD_NP, true, GlobalCols, kPhiPrivate>(r, xr, my, lane, q);
+                    else fwd_path_f32<D, FWD_NP, false, GlobalCols, kPhiPrivate>(r, xr, my, lane, q);
+                } else {
+                    if (has_nan) fwd_path_f32<D, FWD_NP, true, GlobalCols, kPhiAtomic>(r, xr, my, lane, q);
+                    else fwd_path_f32<D, FWD_NP, false, GlobalCols, kPhiAtomic>(r, xr, my, lane, q);
+                }
             }
-        });
+        },
+        priv);
     if (!ok) return false;
     if (rq.phi) {
-        for (int idx = threadIdx.x; idx < 32 * F; idx += blockDim.x) {
-            const int s = idx / F, f = idx - s * F;
-            if (s0 + s < rq.M) {
-                const float v = ps[f * kTileLd + s];
-                if (v != 0.f) atomicAdd(&rq.phi[(s0 + s) * (F + 1) + f], (double)v);
+        if (priv) {
+            for (int idx = lane; idx < 32 * F; idx += 32) {
+                const int s = idx / F, f = idx - s * F;
+                if (sw + s < rq.M) {
+                    const float v = my[f * kTileLd + s];
+                    if (v != 0.f) atomicAdd(&rq.phi[(sw + s) * (F + 1) + f], (double)v);
+                }
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < 32 * F; idx += blockDim.x) {
+                const int s = idx / F, f = idx - s * F;
+                if (s0 + s < rq.M) {
+                    const float v = ps[f * kTileLd + s];
+                    if (v != 0.f) atomicAdd(&rq.phi[(s0 + s) * (F + 1) + f], (double)v);
+                }
             }
         }
     }
@@ -100,15 +173,16 @@ __device__ __forceinline__ bool batch_item(const SegDev& sg, const ReqDev& rq, i
     return true;
 }
 
-// DCLASS: 16 handles widths 1..16, 32 handles 20..32, 64 handles 40..64.
+// Register classes: DCLASS 8 handles widths 1..8 (4 blocks of 128 threads per
+// SM), 12 handles 9..12 (3 blocks), 16 handles 13..16 (2 blocks), 32 handles
+// 20..32 and 64 handles 40..64.
 template <int DCLASS>
-__global__ void __launch_bounds__(128) batch_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(128, DCLASS == 8 ? 4 : (DCLASS == 12 ? 3 : (DCLASS == 16 ? 2 : 1)))
+    batch_kernel(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const size_t rows = a.Fmax + 1;
-    float* xs = (float*)smem;
-    float* gs = xs + rows * kTileLd;
-    float* ps = gs + rows * kTileLd;
-    size_t off = (3 * rows * kTileLd * 4 + 15) & ~(size_t)15;
+    const size_t rows = a.tile_rows;
+    float* ps = (float*)smem;
+    size_t off = (rows * kTileLd * 4 + 15) & ~(size_t)15;
     Rec32* st0 = (Rec32*)(smem + off);
     Rec32* st1 = st0 + (size_t)a.sub * (DCLASS + 1);
     uint64_t* bars = (uint64_t*)(st1 + (size_t)a.sub * (DCLASS + 1));
@@ -137,30 +211,40 @@ __global__ void __launch_bounds__(128) batch_kernel(BatchArgs a) {
         const SegDev sg = a.segs[lo];
         const ReqDev rq = a.reqs[sg.req];
         const int64_t local = item - sg.item_begin;
-        const int64_t s0 = (local % sg.n_tiles) * 32;
+        const int64_t s0 = (local % sg.n_tiles) * (sg.priv ? 32 * kBatchWarps : 32);
         const int64_t p0 = (local / sg.n_tiles) * sg.paths;
         const int64_t p1 = imin64(p0 + sg.paths, sg.n_paths);
         bool ok = true;
-        switch (sg.D) {
 #define QTS_CASE(DD) \
-    case DD: ok = batch_item<DD>(sg, rq, p0, p1, s0, xs, gs, ps, st0, st1, bars, s_phase, &s_flag, a.sub, a.q); break;
-            default: break;
-            QTS_CASE(DCLASS)
-            QTS_CASE((DCLASS == 16 ? 1 : DCLASS == 32 ? 20 : 40))
-            QTS_CASE((DCLASS == 16 ? 2 : DCLASS == 32 ? 24 : 48))
-            QTS_CASE((DCLASS == 16 ? 3 : DCLASS == 32 ? 28 : 56))
-#undef QTS_CASE
-        }
-        if constexpr (DCLASS == 16) {
+    case DD: ok = batch_item<DD>(sg, rq, p0, p1, s0, ps, st0, st1, bars, s_phase, &s_flag, a.sub, a.q); break;
+        if constexpr (DCLASS == 8) {
             switch (sg.D) {
-#define QTS_CASE(DD) \
-    case DD: ok = batch_item<DD>(sg, rq, p0, p1, s0, xs, gs, ps, st0, st1, bars, s_phase, &s_flag, a.sub, a.q); break;
-                QTS_CASE(4) QTS_CASE(5) QTS_CASE(6) QTS_CASE(7) QTS_CASE(8) QTS_CASE(9) QTS_CASE(10)
-                QTS_CASE(11) QTS_CASE(12) QTS_CASE(13) QTS_CASE(14) QTS_CASE(15)
-#undef QTS_CASE
+                QTS_CASE(1) QTS_CASE(2) QTS_CASE(3) QTS_CASE(4) QTS_CASE(5) QTS_CASE(6)
+                QTS_CASE(7) QTS_CASE(8)
+                default: break;
+            }
+        } else if constexpr (DCLASS == 12) {
+            switch (sg.D) {
+                QTS_CASE(9) QTS_CASE(10) QTS_CASE(11) QTS_CASE(12)
+                default: break;
+            }
+        } else if constexpr (DCLASS == 16) {
+            switch (sg.D) {
+                QTS_CASE(13) QTS_CASE(14) QTS_CASE(15) QTS_CASE(16)
+                default: break;
+            }
+        } else if constexpr (DCLASS == 32) {
+            switch (sg.D) {
+                QTS_CASE(20) QTS_CASE(24) QTS_CASE(28) QTS_CASE(32)
+                default: break;
+            }
+        } else {
+            switch (sg.D) {
+                QTS_CASE(40) QTS_CASE(48) QTS_CASE(56) QTS_CASE(64)
                 default: break;
             }
         }
+#undef QTS_CASE
         if (!ok) break;  // a bounded wait ran out: status is set, stop this block
     }
 }
@@ -208,7 +292,7 @@ void batch_forget(const qts_ensemble* e) {
     }
 }
 
-int batch_class(int D) { return D <= 16 ? 16 : (D <= 32 ? 32 : 64); }
+int batch_class(int D) { return D <= 8 ? 8 : D <= 12 ? 12 : (D <= 16 ? 16 : (D <= 32 ? 32 : 64)); }
 
 template <int C>
 static cudaError_t launch_batch_class(const BatchArgs& a, size_t smem, cudaStream_t st, int* blocks_out) {
@@ -224,17 +308,45 @@ static cudaError_t launch_batch_class(const BatchArgs& a, size_t smem, cudaStrea
     return cudaGetLastError();
 }
 
-// paths per work item: about 2^21 FP32 operations per item
+// paths per work item: about 2^23 FP32 operations per item
 static int item_paths(int D, bool grad) {
     const int per_path = 32 * 8 * D * (grad ? 12 : 4);
-    int p = (1 << 21) / std::max(per_path, 1);
-    p = std::max(16, std::min(1024, p));
-    return (p + 15) / 16 * 16;
+    int p = (1 << 23) / std::max(per_path, 1);
+    p = std::max(32, std::min(2048, p));
+    return (p + 31) / 32 * 32;
 }
 
 cudaError_t launch_bwd_epilogue(const qts_ensemble* e, const float* grad, int64_t M, int F,
                                 const double* g_val, const double* g_slot, double* d_leaf,
                                 double* d_z, double* gb, cudaStream_t st);
+
+// Workspace of one request in its ensemble: [adjoint sums (grad only)][XT][GT (grad only)][flag]
+struct BatchWork {
+    size_t grad_bytes, xt_off, gt_off, flag_off, total;
+    int64_t Mpad;
+};
+
+static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+static BatchWork batch_work(const qts_ensemble* e, int64_t M, int F, bool grad) {
+    BatchWork w;
+    w.Mpad = (M + 32 * kBatchWarps - 1) / (32 * kBatchWarps) * (32 * kBatchWarps);
+    w.grad_bytes = grad ? align256(sizeof(double) * (size_t)(4 + e->prep.n_paths + e->prep.n_slots)) : 0;
+    const size_t tbytes = align256(sizeof(float) * (size_t)(F + 1) * (size_t)w.Mpad);
+    w.xt_off = w.grad_bytes;
+    w.gt_off = w.xt_off + tbytes;
+    w.flag_off = w.gt_off + (grad ? tbytes : 0);
+    w.total = w.flag_off + 256;
+    return w;
+}
+
+static cudaError_t launch_transpose(const float* in, int64_t M, int ncols, int64_t ld, float* out, int nrows,
+                                    int64_t Mpad, int* has_nan, cudaStream_t st) {
+    if (Mpad == 0) return cudaSuccess;
+    dim3 grid((unsigned)(Mpad / 32), (unsigned)((nrows + 31) / 32));
+    transpose_pad_kernel<<<grid, dim3(32, 8), 0, st>>>(in, M, ncols, ld, out, nrows, Mpad, has_nan);
+    return cudaGetLastError();
+}
 
 static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, BatchPlan* plan,
                              cudaStream_t cap) {
@@ -245,17 +357,22 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
     };
     std::vector<SegHost> segs;
     std::vector<ReqDev> rd(n);
-    int Fmax = 1;
+    int Fmax = 1, Fpriv = 0;
     for (int r = 0; r < n; ++r) {
         const qts_request& R = reqs[r];
         qts_ensemble* e = R.ens;
-        rd[r] = {R.X, R.grad_phi, R.phi, R.M, R.F, 0, e->d_status};
-        Fmax = std::max(Fmax, R.F);
-        if (R.M <= 0) continue;
         const bool grad = R.grad_phi != nullptr;
+        const BatchWork bw = batch_work(e, R.M, R.F, grad);
+        char* wbase = (char*)e->d_work;
+        rd[r] = {(const float*)(wbase + bw.xt_off), grad ? (const float*)(wbase + bw.gt_off) : nullptr, R.phi,
+                 R.M, bw.Mpad, R.F, 0, (const int*)(wbase + bw.flag_off), e->d_status};
+        const bool priv = R.F + 1 <= kPrivRows;
+        if (priv) Fpriv = std::max(Fpriv, R.F);
+        else Fmax = std::max(Fmax, R.F);
+        if (R.M <= 0) continue;
         double* g_val = grad ? (double*)e->d_work + 4 : nullptr;
         double* g_slot = grad ? g_val + e->prep.n_paths : nullptr;
-        const int n_tiles = (int)((R.M + 31) / 32);
+        const int n_tiles = (int)(priv ? (R.M + 32 * kBatchWarps - 1) / (32 * kBatchWarps) : (R.M + 31) / 32);
         for (const Bucket& b : e->prep.buckets) {
             SegHost s;
             s.d.rec = (const Rec32*)e->d_rec + b.rec_off;
@@ -266,6 +383,8 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
             s.d.paths = e->tuned ? e->tune[b.D].bpaths : item_paths(b.D, grad);
             s.d.n_tiles = n_tiles;
             s.d.req = r;
+            s.d.priv = priv ? 1 : 0;
+            s.d.pad = 0;
             s.cost = (double)s.d.paths * b.D * (grad ? 12 : 4);
             s.cls = batch_class(b.D);
             segs.push_back(s);
@@ -276,7 +395,7 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
         if (a.cls != b.cls) return a.cls < b.cls;
         return a.cost > b.cost;
     });
-    const int sub = 16;
+    const int sub = 32;
     std::vector<int> cls_list;
     std::vector<int64_t> cls_items, cls_first_seg;
     int64_t item = 0;
@@ -316,13 +435,24 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
     cudaError_t err = cudaSuccess;
     for (int r = 0; r < n && err == cudaSuccess; ++r) {
         const qts_request& R = reqs[r];
+        const bool grad = R.grad_phi != nullptr;
+        const BatchWork bw = batch_work(R.ens, R.M, R.F, grad);
+        char* wbase = (char*)R.ens->d_work;
         if (R.phi && R.M > 0) {
             err = launch_phi_init(R.phi, R.M, R.F, R.ens->prep.bias, cap);
             ++kernels;
         }
-        if (R.grad_phi && err == cudaSuccess) {
-            const size_t bytes = sizeof(double) * (size_t)(4 + R.ens->prep.n_paths + R.ens->prep.n_slots);
-            err = cudaMemsetAsync(R.ens->d_work, 0, bytes, cap);
+        if (grad && err == cudaSuccess) err = cudaMemsetAsync(wbase, 0, bw.grad_bytes, cap);
+        if (err == cudaSuccess) err = cudaMemsetAsync(wbase + bw.flag_off, 0, 256, cap);
+        if (R.M > 0 && err == cudaSuccess) {
+            err = launch_transpose(R.X, R.M, R.F, R.F, (float*)(wbase + bw.xt_off), R.F + 1, bw.Mpad,
+                                   (int*)(wbase + bw.flag_off), cap);
+            ++kernels;
+            if (grad && err == cudaSuccess) {
+                err = launch_transpose(R.grad_phi, R.M, R.F + 1, R.F + 1, (float*)(wbase + bw.gt_off), R.F + 1,
+                                       bw.Mpad, nullptr, cap);
+                ++kernels;
+            }
         }
     }
     if (err == cudaSuccess) err = cudaMemsetAsync(d_cnt, 0, cnt_bytes, cap);
@@ -335,12 +465,14 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
         a.reqs = d_reqs;
         a.n_items = cls_items[c];
         a.counter = d_cnt + c;
-        a.Fmax = Fmax;
+        a.tile_rows = std::max(Fmax + 1, Fpriv > 0 ? kBatchWarps * (Fpriv + 1) : 0);
         a.sub = sub;
         a.q = q;
-        const size_t smem = batch_smem_bytes(Fmax, sub, cls);
+        const size_t smem = batch_smem_bytes(a.tile_rows, sub, cls);
         int blocks = 0;
-        if (cls == 16) err = launch_batch_class<16>(a, smem, cap, &blocks);
+        if (cls == 8) err = launch_batch_class<8>(a, smem, cap, &blocks);
+        else if (cls == 12) err = launch_batch_class<12>(a, smem, cap, &blocks);
+        else if (cls == 16) err = launch_batch_class<16>(a, smem, cap, &blocks);
         else if (cls == 32) err = launch_batch_class<32>(a, smem, cap, &blocks);
         else err = launch_batch_class<64>(a, smem, cap, &blocks);
         ++kernels;
@@ -401,12 +533,8 @@ extern "C" qts_status qts_batched_fwd_bwd(int32_t n, const qts_request* reqs, in
     }
     for (int r = 0; r < n; ++r) {
         const qts_request& R = reqs[r];
-        if (!R.grad_phi) continue;
-        void* before = R.ens->d_work;
-        qts_status st = ensure_workspace(
-            R.ens, sizeof(double) * (size_t)(4 + R.ens->prep.n_paths + R.ens->prep.n_slots));
+        qts_status st = ensure_workspace(R.ens, batch_work(R.ens, R.M, R.F, R.grad_phi != nullptr).total);
         if (st != QTS_OK) return st;
-        if (before && before != R.ens->d_work) batch_forget(R.ens);
     }
     std::vector<uint64_t> key;
     key.push_back((uint64_t)n_quad);

@@ -116,8 +116,14 @@ __global__ void __launch_bounds__(256) bwd_kernel(BwdArgs a) {
                 if (has_nan) bwd_path_f64<D, true>(r, xs, gs, lane, a.qd, gsl, gv);
                 else bwd_path_f64<D, false>(r, xs, gs, lane, a.qd, gsl, gv);
             } else {
-                if (has_nan) bwd_path_f32<D, NP, true, WITH_PHI>(r, xs, gs, ps, lane, a.q, gsl, gv);
-                else bwd_path_f32<D, NP, false, WITH_PHI>(r, xs, gs, ps, lane, a.q, gsl, gv);
+                const SmemCols xr{xs, lane}, gr{gs, lane};
+                if constexpr (D <= 16) {
+                    if (has_nan) bwd_path_f32_pk<D, true, WITH_PHI ? kPhiAtomic : kPhiNone>(r, xr, gr, ps, lane, a.q, gsl, gv);
+                    else bwd_path_f32_pk<D, false, WITH_PHI ? kPhiAtomic : kPhiNone>(r, xr, gr, ps, lane, a.q, gsl, gv);
+                } else {
+                    if (has_nan) bwd_path_f32<D, NP, true, WITH_PHI ? kPhiAtomic : kPhiNone, false>(r, xr, gr, ps, lane, a.q, gsl, gv);
+                    else bwd_path_f32<D, NP, false, WITH_PHI ? kPhiAtomic : kPhiNone, false>(r, xr, gr, ps, lane, a.q, gsl, gv);
+                }
             }
         });
     if (!ok) return;

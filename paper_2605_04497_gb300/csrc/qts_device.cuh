@@ -102,7 +102,7 @@ namespace qts {
 // (D elements + 1 header record per path) is copied into two shared staging
 // buffers of `sub` paths each by bulk copies, double-buffered on two
 // mbarriers; warp w calls body(global_path_index, records) for paths
-// w, w + nwarps, ... of each staged sub-chunk.  Thread 0 does the bounded wait
+// w, w + nwarps, ... of each staged sub-chunk (every path, when every_warp).  Thread 0 does the bounded wait
 // and broadcasts the outcome, so the decision to stop is block-uniform.
 // Returns false (after reporting QTS_ERR_TIMEOUT and waiting, bounded, for the
 // copies in flight) if a copy did not complete.  Must be called by all threads;
@@ -110,7 +110,7 @@ namespace qts {
 template <typename Rec, int D, typename Body>
 __device__ __forceinline__ bool stream_paths(const Rec* __restrict__ rec, int64_t p0, int64_t p1, int sub,
                                              Rec* st0, Rec* st1, uint64_t* bars, uint32_t* phase_base,
-                                             int* s_flag, int* status, Body&& body) {
+                                             int* s_flag, int* status, Body&& body, bool every_warp = false) {
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nsub = (int)((p1 - p0 + sub - 1) / sub);
     // phase_base[k] counts completed phases of barrier k before this call, so
@@ -135,7 +135,8 @@ __device__ __forceinline__ bool stream_paths(const Rec* __restrict__ rec, int64_
         const Rec* buf = (c & 1) ? st1 : st0;
         const int64_t q0 = p0 + (int64_t)c * sub;
         const int cnt = (int)imin64(sub, p1 - q0);
-        for (int i = warp; i < cnt; i += nwarps) body(q0 + i, buf + i * (D + 1));
+        const int i0 = every_warp ? 0 : warp, di = every_warp ? 1 : nwarps;
+        for (int i = i0; i < cnt; i += di) body(q0 + i, buf + i * (D + 1));
         __syncthreads();
         if (threadIdx.x == 0 && c + 2 < nsub) issue(c + 2);
     }

@@ -94,8 +94,9 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
                 if (has_nan) fwd_path_f64<D, true>(r, xs, ps, lane, a.qd);
                 else fwd_path_f64<D, false>(r, xs, ps, lane, a.qd);
             } else {
-                if (has_nan) fwd_path_f32<D, NP, true>(r, xs, ps, lane, a.q);
-                else fwd_path_f32<D, NP, false>(r, xs, ps, lane, a.q);
+                const SmemCols xr{xs, lane};
+                if (has_nan) fwd_path_f32<D, NP, true>(r, xr, ps, lane, a.q);
+                else fwd_path_f32<D, NP, false>(r, xr, ps, lane, a.q);
             }
         });
     if (!ok) return;

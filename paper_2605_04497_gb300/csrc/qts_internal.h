@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/qtreeshap.h"
+#include "qtreeshap.h"
 
 namespace qts {
 

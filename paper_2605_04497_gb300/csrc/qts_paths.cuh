@@ -8,6 +8,28 @@
 
 namespace qts {
 
+// How a path adds its phi contributions to the shared tile.
+enum PhiMode : int { kPhiNone = 0, kPhiAtomic = 1, kPhiPrivate = 2 };
+
+template <int MODE>
+__device__ __forceinline__ void phi_add(float* ps, int idx, float v) {
+    if constexpr (MODE == kPhiAtomic) atomicAdd(&ps[idx], v);
+    else if constexpr (MODE == kPhiPrivate) ps[idx] += v;  // tile owned by this warp
+}
+
+// Per-lane reads of one sample's values by feature index.
+struct SmemCols {  // transposed shared tile [feature][kTileLd]; column = lane
+    const float* t;
+    int lane;
+    __device__ __forceinline__ float operator()(int f) const { return t[f * kTileLd + lane]; }
+};
+struct GlobalCols {  // transposed global copy [feature][ld]; this lane's sample = s
+    const float* t;
+    int64_t ld;
+    int64_t s;
+    __device__ __forceinline__ float operator()(int f) const { return __ldg(t + (int64_t)f * ld + s); }
+};
+
 // ====================================================== first order ======
 //
 // c_i = sum_m w_m val prod_{j<i} a_j(t_m) prod_{j>i} a_j(t_m), a_j(t) = z_j + t (o_j - z_j),
@@ -16,9 +38,9 @@ namespace qts {
 // (Thm 1 with S = {i}, Eq. shap_as_weighted_banzhafs).
 
 
-template <int D, int NP, bool HAS_NAN>
-__device__ __forceinline__ void fwd_path_f32(const Rec32* __restrict__ r, const float* __restrict__ xs,
-                                             float* ps, int lane, const QuadF& q) {
+template <int D, int NP, bool HAS_NAN, typename XR, int PHI = kPhiAtomic>
+__device__ __forceinline__ void fwd_path_f32(const Rec32* __restrict__ r, const XR& xr, float* ps, int lane,
+                                             const QuadF& q) {
     constexpr int K = NP / 2;  // node pairs per pass
     const float val = r[0].z;
     float dd[D], zz[D];
@@ -27,7 +49,7 @@ __device__ __forceinline__ void fwd_path_f32(const Rec32* __restrict__ r, const 
     for (int j = 0; j < D; ++j) {
         const Rec32 e = r[1 + j];
         const int f = feat_of(e.bits);
-        const float x = xs[f * kTileLd + lane];
+        const float x = xr(f);
         const bool o = satisfies<HAS_NAN>(x, e.lo, e.hi, e.bits);
         dd[j] = (o ? 1.f : 0.f) - e.z;
         zz[j] = e.z;
@@ -70,7 +92,7 @@ __device__ __forceinline__ void fwd_path_f32(const Rec32* __restrict__ r, const 
         }
     }
 #pragma unroll
-    for (int j = 0; j < D; ++j) atomicAdd(&ps[ff[j] * kTileLd + lane], dd[j] * cacc[j]);
+    for (int j = 0; j < D; ++j) phi_add<PHI>(ps, ff[j] * kTileLd + lane, dd[j] * cacc[j]);
 }
 
 
@@ -144,20 +166,30 @@ __device__ __forceinline__ float transpose_reduce(float (&v)[N], int lane) {
 constexpr int pow2_at_least(int x) { return x <= 1 ? 1 : 2 * pow2_at_least((x + 1) / 2); }
 
 // Reduce dz[0..D) and dval over the warp and add them to the FP64 accumulators.
+// dval rides in the transpose-reduce when D + 1 fits the same power of two,
+// otherwise it gets its own butterfly.
 template <int D, typename T>
 __device__ __forceinline__ void flush_path_grads(T (&dz)[D], T dval, int lane, double* g_slot_p,
                                                  double* g_val_p) {
-    if constexpr (std::is_same<T, float>::value && D + 1 <= 32) {
-        constexpr int N = pow2_at_least(D + 1);
+    if constexpr (std::is_same<T, float>::value && D <= 32) {
+        constexpr int NJ = pow2_at_least(D + 1);
+        constexpr bool JOINT = NJ <= 32 && NJ == pow2_at_least(D);
+        constexpr int N = JOINT ? NJ : pow2_at_least(D);
         constexpr int LOG = (N >= 32) ? 5 : (N >= 16) ? 4 : (N >= 8) ? 3 : (N >= 4) ? 2 : (N >= 2) ? 1 : 0;
         float v[N];
 #pragma unroll
-        for (int i = 0; i < N; ++i) v[i] = i < D ? dz[i] : (i == D ? dval : 0.f);
+        for (int i = 0; i < N; ++i) v[i] = i < D ? dz[i] : ((JOINT && i == D) ? dval : 0.f);
         const float r = transpose_reduce<N>(v, lane);
         const int idx = lane >> (5 - LOG);
         if ((lane & ((1 << (5 - LOG)) - 1)) == 0) {
             if (idx < D) atomicAdd(&g_slot_p[idx], (double)r);
-            else if (idx == D) atomicAdd(g_val_p, (double)r);
+            else if (JOINT && idx == D) atomicAdd(g_val_p, (double)r);
+        }
+        if constexpr (!JOINT) {
+            float x = dval;
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            if (lane == 0) atomicAdd(g_val_p, (double)x);
         }
     } else {
 #pragma unroll
@@ -175,27 +207,30 @@ __device__ __forceinline__ void flush_path_grads(T (&dz)[D], T dval, int lane, d
 
 // ------------------------------------------------------------------ FP32 --
 
-template <int D, int NP, bool HAS_NAN, bool WITH_PHI>
-__device__ __forceinline__ void bwd_path_f32(const Rec32* __restrict__ r, const float* __restrict__ xs,
-                                             const float* __restrict__ gs, float* ps, int lane,
-                                             const QuadF& q, double* g_slot_p, double* g_val_p) {
+// RECOMP: recompute a_j in the backward sweep instead of keeping it in
+// registers (one more FMA per element and node, a third fewer registers).
+template <int D, int NP, bool HAS_NAN, int PHI, bool RECOMP, typename XR, typename GR>
+__device__ __forceinline__ void bwd_path_f32(const Rec32* __restrict__ r, const XR& xr, const GR& gr,
+                                             float* ps, int lane, const QuadF& q, double* g_slot_p,
+                                             double* g_val_p) {
     constexpr int K = NP / 2;
+    constexpr int DA = RECOMP ? 1 : D;
     const float val = r[0].z;
     float dd[D], uu[D], acc1[D], acc2[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
         const Rec32 e = r[1 + j];
         const int f = feat_of(e.bits);
-        const float x = xs[f * kTileLd + lane];
+        const float x = xr(f);
         const bool o = satisfies<HAS_NAN>(x, e.lo, e.hi, e.bits);
         dd[j] = (o ? 1.f : 0.f) - e.z;
-        uu[j] = gs[f * kTileLd + lane] * dd[j];
+        uu[j] = gr(f) * dd[j];
         acc1[j] = 0.f;
         acc2[j] = 0.f;
     }
     const int npass = q.n_pad / NP;
     for (int pass = 0; pass < npass; ++pass) {
-        float2 T[K], C2[K], A[D][K], P[D][K], PU[D][K], S[K], SU[K];
+        float2 T[K], C2[K], A[DA][K], P[D][K], PU[D][K], S[K], SU[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int m = pass * NP + 2 * k;
@@ -209,10 +244,11 @@ __device__ __forceinline__ void bwd_path_f32(const Rec32* __restrict__ r, const 
             const float2 z2 = f2s(r[1 + j].z), d2 = f2s(dd[j]), u2 = f2s(uu[j]);
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                A[j][k] = fma2(T[k], d2, z2);
+                const float2 a = fma2(T[k], d2, z2);
+                if (!RECOMP) A[RECOMP ? 0 : j][k] = a;
                 if (j + 1 < D) {
-                    P[j + 1][k] = mul2(P[j][k], A[j][k]);
-                    PU[j + 1][k] = fma2(PU[j][k], A[j][k], mul2(u2, P[j][k]));
+                    P[j + 1][k] = mul2(P[j][k], a);
+                    PU[j + 1][k] = fma2(PU[j][k], a, mul2(u2, P[j][k]));
                 }
             }
         }
@@ -232,10 +268,16 @@ __device__ __forceinline__ void bwd_path_f32(const Rec32* __restrict__ r, const 
                 a2 = fma2(C2[k], fma2(P[j][k], SU[k], mul2(PU[j][k], S[k])), a2);
             }
             if (j > 0) {
+                float2 z2, d2;
+                if (RECOMP) {
+                    z2 = f2s(r[1 + j].z);
+                    d2 = f2s(dd[j]);
+                }
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
-                    SU[k] = fma2(SU[k], A[j][k], mul2(u2, S[k]));
-                    S[k] = mul2(S[k], A[j][k]);
+                    const float2 a = RECOMP ? fma2(T[k], d2, z2) : A[RECOMP ? 0 : j][k];
+                    SU[k] = fma2(SU[k], a, mul2(u2, S[k]));
+                    S[k] = mul2(S[k], a);
                 }
             }
             acc1[j] += a1.x + a1.y;
@@ -247,8 +289,68 @@ __device__ __forceinline__ void bwd_path_f32(const Rec32* __restrict__ r, const 
     for (int j = 0; j < D; ++j) {
         const int f = feat_of(r[1 + j].bits);
         dval = fmaf(uu[j], acc1[j], dval);
-        dz[j] = val * (acc2[j] - gs[f * kTileLd + lane] * acc1[j]);
-        if constexpr (WITH_PHI) atomicAdd(&ps[f * kTileLd + lane], val * dd[j] * acc1[j]);
+        dz[j] = val * (acc2[j] - gr(f) * acc1[j]);
+        phi_add<PHI>(ps, f * kTileLd + lane, val * dd[j] * acc1[j]);
+    }
+    flush_path_grads<D, float>(dz, dval, lane, g_slot_p, g_val_p);
+}
+
+// Packed variant: one node pair per pass, a_j recomputed, and everything the
+// node loop touches kept as register pairs - {d_j, d_j}, {u_j, u_j} and the two
+// per-element accumulators - so a pass issues only the 12 packed operations per
+// element plus the z reload; the pair halves are added once after all passes.
+template <int D, bool HAS_NAN, int PHI, typename XR, typename GR>
+__device__ __forceinline__ void bwd_path_f32_pk(const Rec32* __restrict__ r, const XR& xr, const GR& gr,
+                                                float* ps, int lane, const QuadF& q, double* g_slot_p,
+                                                double* g_val_p) {
+    const float val = r[0].z;
+    float2 d2[D], u2[D], a1[D], a2[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const Rec32 e = r[1 + j];
+        const int f = feat_of(e.bits);
+        const float x = xr(f);
+        const bool o = satisfies<HAS_NAN>(x, e.lo, e.hi, e.bits);
+        const float d = (o ? 1.f : 0.f) - e.z;
+        d2[j] = f2s(d);
+        u2[j] = f2s(gr(f) * d);
+        a1[j] = f2s(0.f);
+        a2[j] = f2s(0.f);
+    }
+    const int npass = q.n_pad / 2;
+    for (int pass = 0; pass < npass; ++pass) {
+        const int m = 2 * pass;
+        const float2 T = f2(q.t[m], q.t[m + 1]);
+        const float2 C2 = f2(1.f - q.t[m], 1.f - q.t[m + 1]);
+        float2 P[D], PU[D];
+        P[0] = f2(q.w[m], q.w[m + 1]);
+        PU[0] = f2s(0.f);
+#pragma unroll
+        for (int j = 0; j + 1 < D; ++j) {
+            const float2 a = fma2(T, d2[j], f2s(r[1 + j].z));
+            P[j + 1] = mul2(P[j], a);
+            PU[j + 1] = fma2(PU[j], a, mul2(u2[j], P[j]));
+        }
+        float2 S = f2s(1.f), SU = f2s(0.f);
+#pragma unroll
+        for (int j = D - 1; j >= 0; --j) {
+            a1[j] = fma2(P[j], S, a1[j]);
+            a2[j] = fma2(C2, fma2(P[j], SU, mul2(PU[j], S)), a2[j]);
+            if (j > 0) {
+                const float2 a = fma2(T, d2[j], f2s(r[1 + j].z));
+                SU = fma2(SU, a, mul2(u2[j], S));
+                S = mul2(S, a);
+            }
+        }
+    }
+    float dval = 0.f, dz[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const int f = feat_of(r[1 + j].bits);
+        const float c1 = a1[j].x + a1[j].y, c2 = a2[j].x + a2[j].y;
+        dval = fmaf(u2[j].x, c1, dval);
+        dz[j] = val * (c2 - gr(f) * c1);
+        phi_add<PHI>(ps, f * kTileLd + lane, val * d2[j].x * c1);
     }
     flush_path_grads<D, float>(dz, dval, lane, g_slot_p, g_val_p);
 }
