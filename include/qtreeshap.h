@@ -134,6 +134,25 @@ qts_status qts_shap_interactions(qts_ensemble *ens, const float *X, int64_t M, i
                                  int32_t n_quad, float *phi_ij, qts_stream_t stream);
 
 /*
+ * qts_shap_interactions_noalloc - qts_shap_interactions without any device
+ * allocation.  No counterpart in the paper: this is for callers that must not
+ * allocate device memory during the call - code running while a CUDA stream is
+ * being captured into a graph that forbids allocation nodes, services with a
+ * fixed memory budget whose allocator owns all device memory, or latency-bound
+ * callers that cannot afford cudaMalloc's implicit device synchronisation.
+ * The FP64 accumulators live in a fixed array compiled into the library
+ * (16 MiB on every device that loads it, held until the process exits), so the
+ * call supports (F(F-1)/2 + F) * M <= 2,097,152 and returns QTS_ERR_UNSUPPORTED,
+ * with a message, beyond that.  The first call on a device looks the array's
+ * address up (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call clears and reuses the same array, so calls that overlap
+ * on the GPU (different streams, or different threads) race and give wrong
+ * results: serialise them.  Arguments and output layout as qts_shap_interactions.
+ */
+qts_status qts_shap_interactions_noalloc(qts_ensemble *ens, const float *X, int64_t M, int32_t F,
+                                         int32_t n_quad, float *phi_ij, qts_stream_t stream);
+
+/*
  * qts_shap_backward - adjoint of qts_shap_values.  With
  * L = sum_s sum_{f <= F} grad_phi[s][f] * phi[s][f]:
  *   d_leaf  device, N fp64 (N = total nodes), overwritten: dL/d leaf_value[n]

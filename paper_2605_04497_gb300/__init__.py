@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "QTS_OK", 1: "QTS_ERR_ARG", 2: "QTS_ERR_CUDA", 3: "QTS_ERR_OO
 
 # every symbol include/qtreeshap.h declares
 EXPORTS = ("qts_load_ensemble", "qts_update_params", "qts_shap_values", "qts_shap_interactions",
+           "qts_shap_interactions_noalloc",
            "qts_shap_backward", "qts_batched_fwd_bwd", "qts_autotune", "qts_sync_status",
            "qts_get_info", "qts_describe_ensemble", "qts_batched_kernel_count", "qts_batched_last_kernel_ms", "qts_gauss_legendre", "qts_last_error",
            "qts_free")
@@ -68,6 +69,7 @@ def lib():
         L.qts_update_params.argtypes = [vp, vp, vp]
         L.qts_shap_values.argtypes = [vp, vp, i64, i32, i32, vp, vp]
         L.qts_shap_interactions.argtypes = [vp, vp, i64, i32, i32, vp, vp]
+        L.qts_shap_interactions_noalloc.argtypes = [vp, vp, i64, i32, i32, vp, vp]
         L.qts_shap_backward.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, vp]
         L.qts_batched_fwd_bwd.argtypes = [i32, vp, i32, vp]
         L.qts_autotune.argtypes = [vp, vp, i64, i32, ctypes.c_char_p, vp]
@@ -222,6 +224,18 @@ def shap_interactions(ens: Ensemble, X, n_quad: int = 8, out=None, stream=None):
         out = torch.empty((M, F + 1, F + 1), dtype=torch.float32, device=X.device)
     _check(lib().qts_shap_interactions(ens.handle, _ptr(X), M, F, n_quad, _ptr(out),
                                        _stream(stream)))
+    return out
+
+
+def shap_interactions_noalloc(ens: Ensemble, X, out, n_quad: int = 8, stream=None):
+    """Like shap_interactions, for callers that must not allocate device memory
+    during the call: `out` (M x (F+1) x (F+1) float32) is caller-provided and the
+    library's fixed 16 MiB scratch holds the accumulators (see the C header for
+    the size limit and the no-overlap rule)."""
+    _check_x(ens, X)
+    M, F = X.shape
+    _check(lib().qts_shap_interactions_noalloc(ens.handle, _ptr(X), M, F, n_quad, _ptr(out),
+                                               _stream(stream)))
     return out
 
 

@@ -13,6 +13,8 @@
 // FP64 accumulators in the workspace laid out [pair][sample] and
 // [feature][sample]; a finalize kernel writes the (F+1) x (F+1) matrices.
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "qts_device.cuh"
 
@@ -311,6 +313,78 @@ extern "C" qts_status qts_shap_interactions(qts_ensemble* e, const float* X, int
     double* acc_phi = acc_pair + n_pairs * M;
     cudaError_t ce = cudaMemsetAsync(e->d_work, 0, bytes, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "workspace clear");
+    for (const Bucket& b : e->prep.buckets) {
+        ce = launch_int_bucket(e, b, X, M, F, qf, acc_pair, acc_phi, s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "interaction kernel launch");
+    }
+    ce = launch_int_finalize(acc_pair, acc_phi, M, F, e->prep.bias, phi_ij, s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "interaction finalize launch");
+    return QTS_OK;
+}
+
+// ------------------------------------------------- allocation-free variant --
+//
+// Same kernels as qts_shap_interactions, but the FP64 accumulators live in a
+// fixed device array that is part of the library image, so the call never
+// allocates.  Its address is looked up once per device with
+// cudaGetSymbolAddress (host code cannot use the array's name as a device
+// pointer).
+
+namespace qts {
+
+constexpr int64_t kNoAllocDoubles = (int64_t)2 * 1024 * 1024;  // 16 MiB per device
+
+static __device__ __align__(256) double g_int_noalloc_scratch[kNoAllocDoubles];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[64] = {nullptr};
+
+static qts_status noalloc_scratch(void** out) {
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(QTS_ERR_UNSUPPORTED, "device ordinal above 63");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        ce = cudaGetSymbolAddress(&p, g_int_noalloc_scratch);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetSymbolAddress of the interaction scratch");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return QTS_OK;
+}
+
+}  // namespace qts
+
+extern "C" qts_status qts_shap_interactions_noalloc(qts_ensemble* e, const float* X, int64_t M, int32_t F,
+                                                    int32_t n_quad, float* phi_ij, qts_stream_t stream) {
+    qts_status st = check_call(e, X, M, F, n_quad);
+    if (st != QTS_OK) return st;
+    if (M == 0) return QTS_OK;
+    if (!phi_ij) return fail(QTS_ERR_ARG, "phi_ij is NULL");
+    if (e->flags & QTS_FLAG_FP64)
+        return fail(QTS_ERR_UNSUPPORTED, "interactions are computed with the FP32 tables only");
+    if (e->prep.max_unique > 32)
+        return fail(QTS_ERR_UNSUPPORTED, "interactions support paths of at most 32 unique features");
+    const int64_t n_pairs = (int64_t)F * (F - 1) / 2;
+    const int64_t need = (n_pairs + F) * M;
+    if (need > kNoAllocDoubles)
+        return fail(QTS_ERR_UNSUPPORTED,
+                    "qts_shap_interactions_noalloc needs (F(F-1)/2 + F) * M = " + std::to_string(need) +
+                        " accumulator doubles; the fixed scratch holds " + std::to_string(kNoAllocDoubles) +
+                        " (use qts_shap_interactions for larger calls)");
+    cudaStream_t s = (cudaStream_t)stream;
+    QuadF qf;
+    if (!make_quad(n_quad, &qf, nullptr)) return fail(QTS_ERR_ARG, "quadrature rule");
+    void* scratch = nullptr;
+    st = noalloc_scratch(&scratch);
+    if (st != QTS_OK) return st;
+    double* acc_pair = (double*)scratch;
+    double* acc_phi = acc_pair + n_pairs * M;
+    // the array keeps the previous call's sums: clear the part this call uses
+    cudaError_t ce = cudaMemsetAsync(scratch, 0, sizeof(double) * (size_t)need, s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "scratch clear");
     for (const Bucket& b : e->prep.buckets) {
         ce = launch_int_bucket(e, b, X, M, F, qf, acc_pair, acc_phi, s);
         if (ce != cudaSuccess) return cuda_fail(ce, "interaction kernel launch");
