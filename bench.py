@@ -33,6 +33,13 @@ UNIT = "sample·trees/s"
 WORKLOAD = ("batch64: 64 ensembles, trees log-U[10,2000], depth U{3..16}, F log-U[8,200], "
             "M log-U[1,50000], covers from min(100000, 20*2^depth) rows, grad_phi ~N(0,1), seed 20260504")
 N_QUAD = 8
+# DRAM bytes (read + write) of the three persistent launches of one step, from
+# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:batch_kernel -c 3`
+# on this benchmark (profiles/batch_kernel_dram_batch64.md); valid only while the
+# kernel sources hash to KERNEL_HASH, otherwise reported as null.
+TRAFFIC_BYTES = (6.80 + 2.93 + 11.90 + 4.07 + 6.44 + 2.15) * 1e9
+TRAFFIC_HASH = "15e45ed45a795985"
+KERNEL_SOURCES = ("qts_batch.cu", "qts_paths.cuh", "qts_device.cuh", "qts_internal.h")
 # FP32-pipe operations per (sample, merged path element, quadrature node)
 OPS_FUSED = 11   # forward + adjoint in one pass
 OPS_FWD = 4      # forward alone
@@ -56,6 +63,56 @@ def peaks():
             return json.load(fh)
     except Exception:
         return {}
+
+
+def reduce_max(x: float, world: int) -> float:
+    """Max of a per-rank float over the process group (identity at N = 1)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def whole_job_rate(units_per_rank: int, world: int, ms_max: float) -> float:
+    """Units processed by all ranks (replicas) over the slowest rank's time."""
+    return units_per_rank * world / (ms_max / 1e3)
+
+
+def parse_clock_rows(rows):
+    """nvidia-smi rows (index, clocks.sm, clocks.max.sm, power, active mask,
+    hw_slowdown, hw_thermal, sw_thermal, sw_power_cap) -> clock summary."""
+    rows = [r for r in rows if len(r) >= 9]
+    if not rows:
+        return None
+    num = lambda v: v.replace(".", "", 1).isdigit()
+    sm = [float(r[1]) for r in rows if num(r[1])]
+    mx = [float(r[2]) for r in rows if num(r[2])]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+    return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2605_04497_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def fp32_peak_tops(sms: int, mhz: float) -> float:
@@ -93,20 +150,9 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+        rows = [[p.strip() for p in line.split(",")] for line in open(self.path)]
         os.remove(self.path)
-        if not rows:
-            return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+        return parse_clock_rows(rows)
 
 
 # ------------------------------------------------------------------ workload
@@ -167,8 +213,7 @@ def run_ours(args, rank, world, local):
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     kern_ms = []
-    if world > 1:
-        torch.distributed.barrier()
+    barrier(world)
     torch.cuda.synchronize()
     wall0 = time.time()
     for k in range(args.steps):
@@ -181,17 +226,12 @@ def run_ours(args, rank, world, local):
         except qts.QtsError:
             kern_ms.append(None)
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier(world)
     wall = time.time() - wall0
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = float(np.mean(step_ms))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = U * world / (ms / 1e3)
+    ms = reduce_max(float(np.mean(step_ms)), world)
+    value = whole_job_rate(U, world, ms)
     if all(k is not None for k in kern_ms):
         kms, kms_src = float(np.mean(kern_ms)), "CUDA events around the persistent kernel inside the graph"
     else:  # conservative: the whole step (init + persistent kernel + epilogues)
@@ -254,9 +294,12 @@ def run_ours(args, rank, world, local):
                        "paths": int(sum(i["n_paths"] for i in infos)),
                        "n_quad": N_QUAD, "l2": "flushed between steps (256 MB write)",
                        "accumulation": "f64 across path chunks", "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": {"bound": "alu", "kernel": "batch_kernel<12>, batch_kernel<16> (persistent fused forward + adjoint, one per register class)",
+            "roofline": {"bound": "alu",
+                         "kernel": "batch_kernel<8>, <12>, <16> (persistent fused forward + adjoint, one launch per register class)",
                          "achieved": achieved, "peak": peak, "unit": "Tops/s (FP32 pipe lane-ops)",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": TRAFFIC_BYTES if kernel_hash() == TRAFFIC_HASH else None,
+                         "traffic_unit": "bytes per step (the three persistent launches)",
                          "peak_basis": f"{sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (max SM clock)",
                          "algorithmic_ops_per_launch": alg_ops, "kernel_ms": kms,
                          "kernel_ms_source": kms_src},
@@ -295,7 +338,7 @@ def accuracy_check(works, phi, dl, rows_per=2, max_paths=400000):
     return {"max_rel_err_phi": worst, "rows_checked": checked, "tolerance": 1e-5}
 
 
-def cpu_baseline(works, budget_s=20.0, rows=1, trees=2):
+def cpu_baseline(works, budget_s=30.0, rows=2, trees=16):
     """The FP64 oracle (forward + adjoint, exact expansion) on a bounded
     sample: `rows` samples x `trees` trees of every request.  The per
     sample*tree cost of each request is projected to its full M * trees, and the
@@ -340,7 +383,7 @@ def run_reference(args, rank, world):
 
     seed = synth.SEED_BASE + 4
     trees, depth, feats, samples = synth.batch_draw(seed, 64)
-    sample_trees, rows = 2, 1
+    sample_trees, rows = 16, 2
     parts = []
     for e in range(64):
         es = seed * 1000 + e

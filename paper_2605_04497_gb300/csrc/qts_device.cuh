@@ -174,4 +174,22 @@ __device__ __forceinline__ bool load_tile_t(float* tile, const float* __restrict
     return __syncthreads_or(nan_seen) != 0;
 }
 
+// ntiles transposed tiles of 32 rows each (tile w holds rows s0 + 32 w ..),
+// tile w at tile + w * tile_stride, plus `extra` zero rows per tile.
+__device__ __forceinline__ bool load_tiles_t(float* tile, const float* __restrict__ A, int64_t s0, int64_t M,
+                                             int ncols, int64_t ld, int extra, int ntiles, int tile_stride) {
+    int nan_seen = 0;
+    for (int idx = threadIdx.x; idx < 32 * ntiles * ncols; idx += blockDim.x) {
+        const int s = idx / ncols, c = idx - s * ncols;
+        const float v = (s0 + s < M) ? A[(s0 + s) * ld + c] : 0.f;
+        tile[(s >> 5) * tile_stride + c * kTileLd + (s & 31)] = v;
+        nan_seen |= (v != v);
+    }
+    for (int idx = threadIdx.x; idx < ntiles * extra * kTileLd; idx += blockDim.x) {
+        const int w = idx / (extra * kTileLd), r = idx - w * extra * kTileLd;
+        tile[w * tile_stride + ncols * kTileLd + r] = 0.f;
+    }
+    return __syncthreads_or(nan_seen) != 0;
+}
+
 }  // namespace qts

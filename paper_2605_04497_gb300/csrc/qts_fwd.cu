@@ -28,6 +28,9 @@ struct FwdArgs {
     int F;
     double* phi;        // M x (F+1)
     int* status;
+    int ntiles;         // sample tiles of 32 per block: 1 (warps share the tile and
+                        // split paths, atomics) or the warp count (each warp owns a
+                        // tile and walks every path; private phi tile, no atomics)
     QuadF q;
     QuadD qd;
 };
@@ -35,16 +38,16 @@ struct FwdArgs {
 // --------------------------------------------------------------- kernel ---
 
 template <typename Rec, typename Acc>
-__device__ __forceinline__ size_t fwd_smem_layout(int F, int sub, int D, float** xs, Acc** ps,
+__device__ __forceinline__ size_t fwd_smem_layout(int F, int sub, int D, int ntiles, float** xs, Acc** ps,
                                                   Rec** stage0, Rec** stage1, uint64_t** bars,
                                                   unsigned char* base) {
     const int rows = F + 1;
     size_t off = 0;
     *xs = (float*)(base + off);
-    off += (size_t)rows * kTileLd * sizeof(float);
+    off += (size_t)ntiles * rows * kTileLd * sizeof(float);
     off = (off + 15) & ~(size_t)15;
     *ps = (Acc*)(base + off);
-    off += (size_t)rows * kTileLd * sizeof(Acc);
+    off += (size_t)ntiles * rows * kTileLd * sizeof(Acc);
     off = (off + 15) & ~(size_t)15;
     *stage0 = (Rec*)(base + off);
     off += (size_t)sub * (D + 1) * sizeof(Rec);
@@ -65,17 +68,22 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
     Acc* ps;
     Rec *st0, *st1;
     uint64_t* bars;
-    fwd_smem_layout<Rec, Acc>(a.F, a.sub, D, &xs, &ps, &st0, &st1, &bars, smem);
+    fwd_smem_layout<Rec, Acc>(a.F, a.sub, D, a.ntiles, &xs, &ps, &st0, &st1, &bars, smem);
     __shared__ int s_flag;
     __shared__ uint32_t s_phase[2];
 
     const int F = a.F;
-    const int lane = threadIdx.x & 31;
-    const int tile = (int)(blockIdx.x % (unsigned)a.n_tiles);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool priv = a.ntiles > 1;
+    const int stride = (F + 1) * kTileLd;
+    const int group = (int)(blockIdx.x % (unsigned)a.n_tiles);
     const int64_t chunk = blockIdx.x / (unsigned)a.n_tiles;
-    const int64_t s0 = (int64_t)tile * 32;
+    const int64_t s0 = (int64_t)group * 32 * a.ntiles;
     const int64_t p0 = chunk * a.paths_per_block;
     const int64_t p1 = imin64(p0 + a.paths_per_block, a.n_paths);
+    float* my_xs = priv ? xs + warp * stride : xs;
+    Acc* my_ps = priv ? ps + warp * stride : ps;
+    const int64_t sw = priv ? s0 + 32 * warp : s0;
 
     if (threadIdx.x == 0) {
         mbar_init(&bars[0], 1);
@@ -83,28 +91,45 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
         mbar_fence_init();
         s_phase[0] = s_phase[1] = 0;
     }
-    for (int idx = threadIdx.x; idx < (F + 1) * kTileLd; idx += blockDim.x) ps[idx] = (Acc)0;
-    // sample tile (row = feature, column = sample) plus a zero row F for padding
-    const bool has_nan = load_tile_t(xs, a.X, s0, a.M, F, F, 1);
+    for (int idx = threadIdx.x; idx < a.ntiles * stride; idx += blockDim.x) ps[idx] = (Acc)0;
+    // sample tiles (row = feature, column = sample) plus a zero row F for padding
+    const bool has_nan = load_tiles_t(xs, a.X, s0, a.M, F, F, 1, a.ntiles, stride);
 
     const bool ok = stream_paths<Rec, D>(
         (const Rec*)a.rec, p0, p1, a.sub, st0, st1, bars, s_phase, &s_flag, a.status,
         [&](int64_t, const Rec* r) {
             if constexpr (FP64) {
-                if (has_nan) fwd_path_f64<D, true>(r, xs, ps, lane, a.qd);
-                else fwd_path_f64<D, false>(r, xs, ps, lane, a.qd);
+                if (has_nan) fwd_path_f64<D, true>(r, my_xs, my_ps, lane, a.qd);
+                else fwd_path_f64<D, false>(r, my_xs, my_ps, lane, a.qd);
             } else {
-                const SmemCols xr{xs, lane};
-                if (has_nan) fwd_path_f32<D, NP, true>(r, xr, ps, lane, a.q);
-                else fwd_path_f32<D, NP, false>(r, xr, ps, lane, a.q);
+                const SmemCols xr{my_xs, lane};
+                if (priv) {
+                    if (has_nan) fwd_path_f32<D, NP, true, SmemCols, kPhiPrivate>(r, xr, my_ps, lane, a.q);
+                    else fwd_path_f32<D, NP, false, SmemCols, kPhiPrivate>(r, xr, my_ps, lane, a.q);
+                } else {
+                    if (has_nan) fwd_path_f32<D, NP, true, SmemCols, kPhiAtomic>(r, xr, my_ps, lane, a.q);
+                    else fwd_path_f32<D, NP, false, SmemCols, kPhiAtomic>(r, xr, my_ps, lane, a.q);
+                }
             }
-        });
+        },
+        priv);
     if (!ok) return;
-    for (int idx = threadIdx.x; idx < 32 * F; idx += blockDim.x) {
-        const int s = idx / F, f = idx - s * F;
-        if (s0 + s < a.M) {
-            const Acc v = ps[f * kTileLd + s];
-            if (v != (Acc)0) atomicAdd(&a.phi[(s0 + s) * (F + 1) + f], (double)v);
+    const int nflush = 32 * F;
+    if (priv) {
+        for (int idx = lane; idx < nflush; idx += 32) {
+            const int s = idx / F, f = idx - s * F;
+            if (sw + s < a.M) {
+                const Acc v = my_ps[f * kTileLd + s];
+                if (v != (Acc)0) atomicAdd(&a.phi[(sw + s) * (F + 1) + f], (double)v);
+            }
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < nflush; idx += blockDim.x) {
+            const int s = idx / F, f = idx - s * F;
+            if (s0 + s < a.M) {
+                const Acc v = ps[f * kTileLd + s];
+                if (v != (Acc)0) atomicAdd(&a.phi[(s0 + s) * (F + 1) + f], (double)v);
+            }
         }
     }
 }
@@ -152,11 +177,11 @@ static cudaError_t launch_fwd_d(const FwdArgs& a, int np, bool fp64, int warps, 
     return launch_fwd_t<D, 2, false>(a, warps, blocks, smem, st);
 }
 
-size_t fwd_smem_bytes(int F, int sub, int D, bool fp64) {
+size_t fwd_smem_bytes(int F, int sub, int D, bool fp64, int ntiles) {
     const size_t rows = F + 1;
-    size_t off = rows * kTileLd * 4;
+    size_t off = ntiles * rows * kTileLd * 4;
     off = (off + 15) & ~(size_t)15;
-    off += rows * kTileLd * (fp64 ? 8 : 4);
+    off += ntiles * rows * kTileLd * (fp64 ? 8 : 4);
     off = (off + 15) & ~(size_t)15;
     off += 2 * (size_t)sub * (D + 1) * (fp64 ? sizeof(Rec64) : sizeof(Rec32));
     off = (off + 15) & ~(size_t)15;
@@ -174,7 +199,10 @@ cudaError_t launch_fwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
     a.n_paths = b.n_paths;
     a.sub = std::max(1, tn.sub);
     a.paths_per_block = std::max<int64_t>(a.sub, (int64_t)tn.paths / a.sub * a.sub);
-    a.n_tiles = (int)((M + 31) / 32);
+    const int warps = std::max(1, std::min(8, tn.warps));
+    // private tiles when the per-warp X and phi tiles stay small
+    a.ntiles = (!fp64 && tn.priv && fwd_smem_bytes(F, a.sub, b.D, false, warps) <= 100 * 1024) ? warps : 1;
+    a.n_tiles = (int)((M + 32 * a.ntiles - 1) / (32 * a.ntiles));
     a.X = X;
     a.M = M;
     a.F = F;
@@ -185,8 +213,8 @@ cudaError_t launch_fwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
     const int64_t chunks = (b.n_paths + a.paths_per_block - 1) / a.paths_per_block;
     const int64_t blocks = chunks * a.n_tiles;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const size_t smem = fwd_smem_bytes(F, a.sub, b.D, fp64);
-    const int warps = std::max(1, std::min(8, tn.warps));
+    const size_t smem = fwd_smem_bytes(F, a.sub, b.D, fp64, a.ntiles);
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     switch (b.D) {
 #define QTS_CASE(DD) \
     case DD: return launch_fwd_d<DD>(a, tn.np, fp64, warps, blocks, smem, st);

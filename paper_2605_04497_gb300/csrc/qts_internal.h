@@ -85,6 +85,7 @@ struct Tune {
     int sub = 32;         // paths per staged sub-chunk
     int np = 8;           // nodes per register pass (8, 4 or 2)
     int bpaths = 128;     // paths per work item of the fused forward + adjoint pass
+    int priv = 1;         // forward: let each warp own a sample tile when it fits
 };
 
 }  // namespace qts

@@ -1,5 +1,6 @@
 // Launch-shape autotuner: for each bucket width of an ensemble, time candidate
-// (warps per block, paths per block, staged sub-chunk, node-group width) of the
+// (warps per block, paths per block, staged sub-chunk, node-group width, private
+// per-warp tiles or not) of the
 // forward kernel and candidate work-item sizes of the fused forward+adjoint
 // kernel on the caller's data, keep the fastest, and optionally merge them into
 // a JSON cache keyed by (width, log2 F, log2 M).
@@ -29,7 +30,8 @@ static std::string cache_key(int D, int F, int64_t M) {
     return std::to_string(D) + "|" + std::to_string(ilog2(F)) + "|" + std::to_string(ilog2(std::max<int64_t>(M, 1)));
 }
 
-// The cache file is a flat JSON object: {"D|logF|logM": [warps, paths, sub, np, bpaths], ...}
+// The cache file is a flat JSON object:
+//   {"D|logF|logM": [warps, paths, sub, np, bpaths, priv], ...}
 static std::map<std::string, Tune> read_cache(const char* path) {
     std::map<std::string, Tune> out;
     std::ifstream in(path);
@@ -44,12 +46,12 @@ static std::map<std::string, Tune> read_cache(const char* path) {
         const std::string key = s.substr(i + 1, j - i - 1);
         const size_t lb = s.find('[', j), rb = s.find(']', j);
         if (lb == std::string::npos || rb == std::string::npos) break;
-        int v[5] = {0, 0, 0, 0, 0};
+        int v[6] = {0, 0, 0, 0, 0, 0};
         std::stringstream vs(s.substr(lb + 1, rb - lb - 1));
         std::string tok;
         int k = 0;
-        while (k < 5 && std::getline(vs, tok, ',')) v[k++] = std::atoi(tok.c_str());
-        if (k == 5) out[key] = Tune{v[0], v[1], v[2], v[3], v[4]};
+        while (k < 6 && std::getline(vs, tok, ',')) v[k++] = std::atoi(tok.c_str());
+        if (k == 6) out[key] = Tune{v[0], v[1], v[2], v[3], v[4], v[5]};
         i = rb + 1;
     }
     return out;
@@ -62,7 +64,7 @@ static void write_cache(const char* path, const std::map<std::string, Tune>& m) 
     for (const auto& kv : m) {
         const Tune& t = kv.second;
         o << "  \"" << kv.first << "\": [" << t.warps << ", " << t.paths << ", " << t.sub << ", " << t.np
-          << ", " << t.bpaths << "]" << (++n < m.size() ? "," : "") << "\n";
+          << ", " << t.bpaths << ", " << t.priv << "]" << (++n < m.size() ? "," : "") << "\n";
     }
     o << "}\n";
     o.close();
@@ -142,11 +144,13 @@ extern "C" qts_status qts_autotune(qts_ensemble* e, const float* X, int64_t M, i
             for (int warps : {2, 4, 8}) {
                 for (int paths : {128, 512, 2048}) {
                     for (int sub : {16, 32}) {
+                      for (int priv : {1, 0}) {
                         Tune t = best;
                         t.np = np;
                         t.warps = warps;
                         t.paths = paths;
                         t.sub = sub;
+                        t.priv = priv;
                         cudaError_t le = cudaSuccess;
                         const float ms = time_ms([&] {
                             le = launch_fwd_bucket(e, b, X, Mt, F, qf, qd, phi, t, s);
@@ -156,6 +160,7 @@ extern "C" qts_status qts_autotune(qts_ensemble* e, const float* X, int64_t M, i
                             best = t;
                         }
                         cudaGetLastError();
+                      }
                     }
                 }
             }
