@@ -63,6 +63,7 @@ typedef enum qts_status {
 #define QTS_MAX_UNIQUE_FEATURES_PER_PATH 64
 #define QTS_MAX_FEATURES 640 /* sample and accumulator tiles live in shared memory */
 #define QTS_MAX_QUAD 32
+#define QTS_MAX_FEATURES_ORDER3 128
 
 /*
  * qts_load_ensemble - copy a tree ensemble and build its path tables.
@@ -132,6 +133,21 @@ qts_status qts_shap_values(qts_ensemble *ens, const float *X, int64_t M, int32_t
  */
 qts_status qts_shap_interactions(qts_ensemble *ens, const float *X, int64_t M, int32_t F,
                                  int32_t n_quad, float *phi_ij, qts_stream_t stream);
+
+/*
+ * qts_shap_interactions3 - third-order Shapley interaction indices (Thm 1 with
+ * S = {i, j, k}; Alg. 1 with s = 3; the paper's any-order construction):
+ *   SII_ijk = sum_v val (o_i - z_i)(o_j - z_j)(o_k - z_k) int_0^1 prod_{l not in {i,j,k}} a_l(p) dp
+ * n_quad points are exact for paths of at most 2 n_quad + 2 unique features
+ * (Thm 2).  Output, compact and symmetric-free:
+ *   sii3   device, M x C(F,3) fp32, overwritten; entry [s][t] for the triple
+ *          a < b < c with t = (C(F,3) - C(F-a,3)) + (C(F-a-1,2) - C(F-b,2)) + (c-b-1)
+ * Cross-path accumulation is FP64 in the ensemble's workspace (C(F,3) * M
+ * doubles, grown on demand with cudaMalloc).  F <= QTS_MAX_FEATURES_ORDER3,
+ * paths of at most 16 unique features, FP32 tables only.
+ */
+qts_status qts_shap_interactions3(qts_ensemble *ens, const float *X, int64_t M, int32_t F,
+                                  int32_t n_quad, float *sii3, qts_stream_t stream);
 
 /*
  * qts_shap_interactions_noalloc - qts_shap_interactions without any device

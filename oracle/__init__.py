@@ -67,8 +67,11 @@ def _load():
         lib.orc_alg1.argtypes = [E, vp, i32, i32, vp]
         lib.orc_grad_exact.argtypes = [E, vp, i64, vp, vp, i64, i32, vp, vp]
         lib.orc_path_stats.argtypes = [E, vp, vp, vp]
+        lib.orc_sii3_exact.argtypes = [E, vp, i64, i32, vp]
+        lib.orc_brute_force3.argtypes = [E, vp, vp]
         for f in ("orc_gl_nodes", "orc_shap_exact", "orc_sii_exact", "orc_shap_quad",
-                  "orc_brute_force", "orc_alg1", "orc_grad_exact", "orc_path_stats"):
+                  "orc_brute_force", "orc_alg1", "orc_grad_exact", "orc_path_stats",
+                  "orc_sii3_exact", "orc_brute_force3"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -183,10 +186,28 @@ def brute_force(ens, x):
     return phi, sii
 
 
+def sii3_exact(ens, X, n_threads: int | None = None) -> np.ndarray:
+    """Third-order SII: M x F x F x F, symmetric, zero where indices repeat."""
+    b = _Bound(ens)
+    X = _f32(X, b.F)
+    out = np.zeros((X.shape[0], b.F, b.F, b.F))
+    _check(_load().orc_sii3_exact(b.ref(), X.ctypes.data, X.shape[0], n_threads or threads(),
+                                  out.ctypes.data), "orc_sii3_exact")
+    return out
+
+
+def brute_force3(ens, x) -> np.ndarray:
+    b = _Bound(ens)
+    x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1)
+    out = np.zeros((b.F, b.F, b.F))
+    _check(_load().orc_brute_force3(b.ref(), x.ctypes.data, out.ctypes.data), "orc_brute_force3")
+    return out
+
+
 def alg1(ens, x, order: int, n: int) -> np.ndarray:
     b = _Bound(ens)
     x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1)
-    out = np.zeros(b.F + 1 if order == 1 else (b.F, b.F))
+    out = np.zeros(b.F + 1 if order == 1 else ((b.F, b.F) if order == 2 else (b.F, b.F, b.F)))
     _check(_load().orc_alg1(b.ref(), x.ctypes.data, order, n, out.ctypes.data), "orc_alg1")
     return out
 

@@ -631,7 +631,7 @@ static void alg1_dfs(alg1_ctx *C, int32_t v, const double *c, double wprod, doub
             double acc = 0.0;
             for (int m = 0; m < n; ++m) acc += C->w[m] * Hu[m] * delta[m];
             C->out[f] += acc;
-        } else {
+        } else if (C->order == 2) {
             for (int j = 0; j < C->F; ++j) {
                 if (j == f || !C->seen[j]) continue;
                 double aj = C->p[j] - 1.0, acc = 0.0;
@@ -639,6 +639,26 @@ static void alg1_dfs(alg1_ctx *C, int32_t v, const double *c, double wprod, doub
                     acc += C->w[m] * Hu[m] * delta[m] * (aj / (1.0 + aj * C->t[m]));
                 C->out[j * C->F + f] += acc;
                 C->out[f * C->F + j] += acc;
+            }
+        } else {
+            /* s = 3: every 2-subset {j, k} of the active set without f */
+            const int F = C->F;
+            for (int j = 0; j < F; ++j) {
+                if (j == f || !C->seen[j]) continue;
+                for (int k = j + 1; k < F; ++k) {
+                    if (k == f || !C->seen[k]) continue;
+                    double aj = C->p[j] - 1.0, ak = C->p[k] - 1.0, acc = 0.0;
+                    for (int m = 0; m < n; ++m)
+                        acc += C->w[m] * Hu[m] * delta[m] * (aj / (1.0 + aj * C->t[m])) *
+                               (ak / (1.0 + ak * C->t[m]));
+                    int64_t F2 = (int64_t)F * F;
+                    C->out[j * F2 + k * F + f] += acc;
+                    C->out[j * F2 + f * F + k] += acc;
+                    C->out[k * F2 + j * F + f] += acc;
+                    C->out[k * F2 + f * F + j] += acc;
+                    C->out[f * F2 + j * F + k] += acc;
+                    C->out[f * F2 + k * F + j] += acc;
+                }
             }
         }
         C->p[f] = pold;
@@ -655,7 +675,7 @@ static double tree_bias(const orc_ens *e, int64_t base, int32_t v) {
 }
 
 int orc_alg1(const orc_ens *e, const float *x, int order, int n, double *out) {
-    if (order != 1 && order != 2) return -1;
+    if (order < 1 || order > 3) return -1;
     alg1_ctx *C = (alg1_ctx *)calloc(1, sizeof(alg1_ctx));
     if (!C) return -1;
     if (orc_gl_nodes(n, C->t, C->w)) { free(C); return -1; }
@@ -663,7 +683,7 @@ int orc_alg1(const orc_ens *e, const float *x, int order, int n, double *out) {
     C->e = e; C->x = x; C->order = order; C->n = n; C->F = F; C->out = out;
     C->p = (double *)calloc((size_t)F, sizeof(double));
     C->seen = (int *)calloc((size_t)F, sizeof(int));
-    int64_t nout = order == 1 ? F + 1 : (int64_t)F * F;
+    int64_t nout = order == 1 ? F + 1 : (order == 2 ? (int64_t)F * F : (int64_t)F * F * F);
     for (int64_t k = 0; k < nout; ++k) out[k] = 0.0;
     double ones[256], H[256];
     for (int m = 0; m < n; ++m) ones[m] = 1.0;
@@ -815,5 +835,100 @@ int orc_grad_exact(const orc_ens *e, const float *X, int64_t M, const float *gra
     }
     free(th); free(jobs); free(dval); free(dz); free(plist);
     free_paths(&P);
+    return 0;
+}
+
+/* ================================================== third order (|S| = 3) */
+
+/* Thm 1 with S = {i, j, k}: SII_ijk = int_0^1 val (o_i - z_i)(o_j - z_j)(o_k - z_k)
+ * prod_{l not in {i,j,k}} a_l(p) dp (Eq. ao_shap_is_intergral_of_ao_banzhaf). */
+static void *sii3_exact_worker(void *arg) {
+    job_t *J = (job_t *)arg;
+    const paths_t *P = J->P;
+    int F = J->F;
+    int64_t F2 = (int64_t)F * F, F3 = F2 * F;
+    int dmax = P->max_d > 0 ? P->max_d : 1;
+    double *o = (double *)malloc(sizeof(double) * dmax);
+    double *zz = (double *)malloc(sizeof(double) * dmax);
+    double *oo = (double *)malloc(sizeof(double) * dmax);
+    double *scr = (double *)malloc(sizeof(double) * 2 * (dmax + 1));
+    for (int64_t s = J->s_begin; s < J->s_end; ++s) {
+        const float *x = J->X + s * F;
+        double *out = J->sii + s * F3;
+        for (int64_t q = 0; q < F3; ++q) out[q] = 0.0;
+        for (int64_t p = 0; p < P->n_paths; ++p) {
+            const ppath *pp = &P->p[p];
+            const pelem *el = P->el + pp->el_begin;
+            int d = pp->d;
+            for (int j = 0; j < d; ++j) o[j] = satisfied(&el[j], x);
+            for (int i = 0; i < d; ++i)
+                for (int j = i + 1; j < d; ++j)
+                    for (int k = j + 1; k < d; ++k) {
+                        int n = 0;
+                        for (int l = 0; l < d; ++l) {
+                            if (l == i || l == j || l == k) continue;
+                            zz[n] = el[l].z;
+                            oo[n] = o[l];
+                            ++n;
+                        }
+                        double I = bernstein_integral(zz, oo, n, scr);
+                        double v = pp->val * (o[i] - el[i].z) * (o[j] - el[j].z) * (o[k] - el[k].z) * I;
+                        int a = el[i].feat, b = el[j].feat, c = el[k].feat;
+                        out[a * F2 + b * F + c] += v; out[a * F2 + c * F + b] += v;
+                        out[b * F2 + a * F + c] += v; out[b * F2 + c * F + a] += v;
+                        out[c * F2 + a * F + b] += v; out[c * F2 + b * F + a] += v;
+                    }
+        }
+    }
+    free(o); free(zz); free(oo); free(scr);
+    return NULL;
+}
+
+int orc_sii3_exact(const orc_ens *e, const float *X, int64_t M, int n_threads, double *sii3) {
+    paths_t P;
+    if (build_paths(e, &P)) return -1;
+    job_t proto;
+    memset(&proto, 0, sizeof(proto));
+    proto.e = e; proto.P = &P; proto.X = X; proto.F = e->n_features; proto.sii = sii3;
+    int rc = run_threads(sii3_exact_worker, &proto, M, n_threads);
+    free_paths(&P);
+    return rc;
+}
+
+/* SII_ijk = sum_{T subset of [F]\{i,j,k}} |T|! (F-|T|-3)! / (F-2)! Delta_ijk f(T),
+ * Delta_ijk f(T) = sum_{L subset of {i,j,k}} (-1)^(3-|L|) f(T + L)  (App. C, |S| = 3). */
+int orc_brute_force3(const orc_ens *e, const float *x, double *sii3) {
+    int F = e->n_features;
+    if (F < 3 || F > 16) return -1;
+    uint32_t NS = 1u << F;
+    double *fs = (double *)malloc(sizeof(double) * NS);
+    if (!fs) return -1;
+    for (uint32_t S = 0; S < NS; ++S) {
+        double acc = 0.0;
+        for (int t = 0; t < e->n_trees; ++t) acc += game(e, e->node_offsets[t], 0, x, S);
+        fs[S] = acc;
+    }
+    double fact[32];
+    fact[0] = 1.0;
+    for (int k = 1; k < 32; ++k) fact[k] = fact[k - 1] * (double)k;
+    int64_t F2 = (int64_t)F * F;
+    for (int64_t q = 0; q < F2 * F; ++q) sii3[q] = 0.0;
+    for (int i = 0; i < F; ++i)
+        for (int j = i + 1; j < F; ++j)
+            for (int k = j + 1; k < F; ++k) {
+                uint32_t mi = 1u << i, mj = 1u << j, mk = 1u << k, mall = mi | mj | mk;
+                double acc = 0.0;
+                for (uint32_t T = 0; T < NS; ++T) {
+                    if (T & mall) continue;
+                    int t = __builtin_popcount(T);
+                    double delta = fs[T | mall] - fs[T | mi | mj] - fs[T | mi | mk] - fs[T | mj | mk] +
+                                   fs[T | mi] + fs[T | mj] + fs[T | mk] - fs[T];
+                    acc += fact[t] * fact[F - t - 3] / fact[F - 2] * delta;
+                }
+                sii3[i * F2 + j * F + k] = acc; sii3[i * F2 + k * F + j] = acc;
+                sii3[j * F2 + i * F + k] = acc; sii3[j * F2 + k * F + i] = acc;
+                sii3[k * F2 + i * F + j] = acc; sii3[k * F2 + j * F + i] = acc;
+            }
+    free(fs);
     return 0;
 }

@@ -12,9 +12,11 @@
  *   orc_sii_exact       pairwise SII_ij the same way (Thm 1 with |S|=2).
  *   orc_shap_quad       phi_i with n-point Gauss-Legendre instead of the exact
  *                       integral (Eq. shap_as_weighted_banzhafs).
+ *   orc_sii3_exact      third-order SII_ijk the same way (Thm 1 with |S|=3).
  *   orc_brute_force     phi_i and SII_ij by subset enumeration of the
  *                       Path-Dependent game (Eq. path_dependent_game, App. C).
- *   orc_alg1            Algorithm 1 (DFS with telescoping, orders 1 and 2).
+ *   orc_brute_force3    SII_ijk by subset enumeration.
+ *   orc_alg1            Algorithm 1 (DFS with telescoping, orders 1, 2 and 3).
  *   orc_grad_exact      d(sum grad_phi*phi)/d(leaf values) and /d(edge weights),
  *                       differentiating Thm 1 analytically (no paper passage;
  *                       pinned by finite differences of the brute force).
@@ -63,8 +65,16 @@ int orc_shap_quad(const orc_ens *e, const float *X, int64_t M, int n, int n_thre
 /* One sample; needs n_features <= 20.  phi: F+1, sii: F x F (may be NULL). */
 int orc_brute_force(const orc_ens *e, const float *x, double *phi, double *sii);
 
+/* Third-order SII_ijk (Thm 1 with |S| = 3) integrated exactly; sii3 is
+ * M x F x F x F, symmetric, zero wherever two indices coincide. */
+int orc_sii3_exact(const orc_ens *e, const float *X, int64_t M, int n_threads, double *sii3);
+
+/* Third-order SII for one sample by subset enumeration; 3 <= F <= 16. */
+int orc_brute_force3(const orc_ens *e, const float *x, double *sii3);
+
 /* Algorithm 1 on one sample with n Gauss-Legendre points; order 1 fills phi
- * (F+1 incl. E[f]), order 2 fills sii (F x F, symmetric, zero diagonal). */
+ * (F+1 incl. E[f]), order 2 fills sii (F x F, symmetric, zero diagonal),
+ * order 3 fills F x F x F (symmetric, zero where indices coincide). */
 int orc_alg1(const orc_ens *e, const float *x, int order, int n, double *out);
 
 /* L = sum_s sum_{f<=F} grad_phi[s,f] * phi[s,f].  Writes dL/d leaf_value and

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "QTS_OK", 1: "QTS_ERR_ARG", 2: "QTS_ERR_CUDA", 3: "QTS_ERR_OO
 
 # every symbol include/qtreeshap.h declares
 EXPORTS = ("qts_load_ensemble", "qts_update_params", "qts_shap_values", "qts_shap_interactions",
-           "qts_shap_interactions_noalloc",
+           "qts_shap_interactions_noalloc", "qts_shap_interactions3",
            "qts_shap_backward", "qts_batched_fwd_bwd", "qts_autotune", "qts_sync_status",
            "qts_get_info", "qts_describe_ensemble", "qts_batched_kernel_count", "qts_batched_last_kernel_ms", "qts_gauss_legendre", "qts_last_error",
            "qts_free")
@@ -70,6 +70,7 @@ def lib():
         L.qts_shap_values.argtypes = [vp, vp, i64, i32, i32, vp, vp]
         L.qts_shap_interactions.argtypes = [vp, vp, i64, i32, i32, vp, vp]
         L.qts_shap_interactions_noalloc.argtypes = [vp, vp, i64, i32, i32, vp, vp]
+        L.qts_shap_interactions3.argtypes = [vp, vp, i64, i32, i32, vp, vp]
         L.qts_shap_backward.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, vp]
         L.qts_batched_fwd_bwd.argtypes = [i32, vp, i32, vp]
         L.qts_autotune.argtypes = [vp, vp, i64, i32, ctypes.c_char_p, vp]
@@ -236,6 +237,42 @@ def shap_interactions_noalloc(ens: Ensemble, X, out, n_quad: int = 8, stream=Non
     M, F = X.shape
     _check(lib().qts_shap_interactions_noalloc(ens.handle, _ptr(X), M, F, n_quad, _ptr(out),
                                                _stream(stream)))
+    return out
+
+
+def triple_index(F: int):
+    """Compact index of each triple a < b < c (the layout of shap_interactions3)."""
+    from math import comb
+
+    idx = {}
+    for a in range(F):
+        for b in range(a + 1, F):
+            for c in range(b + 1, F):
+                idx[(a, b, c)] = (comb(F, 3) - comb(F - a, 3)) + (comb(F - a - 1, 2) - comb(F - b, 2)) + (c - b - 1)
+    return idx
+
+
+def shap_interactions3(ens: Ensemble, X, n_quad: int = 8, out=None, stream=None):
+    """Third-order SII, compact: M x C(F,3) float32 over triples a < b < c."""
+    import torch
+    from math import comb
+
+    _check_x(ens, X)
+    M, F = X.shape
+    if out is None:
+        out = torch.empty((M, comb(F, 3)), dtype=torch.float32, device=X.device)
+    _check(lib().qts_shap_interactions3(ens.handle, _ptr(X), M, F, n_quad, _ptr(out), _stream(stream)))
+    return out
+
+
+def expand_triples(compact, F: int):
+    """Dense symmetric M x F x F x F array (numpy) from the compact layout."""
+    c = np.asarray(compact)
+    out = np.zeros((c.shape[0], F, F, F), dtype=c.dtype)
+    for (a, b, cc), t in triple_index(F).items():
+        v = c[:, t]
+        for i, j, k in ((a, b, cc), (a, cc, b), (b, a, cc), (b, cc, a), (cc, a, b), (cc, b, a)):
+            out[:, i, j, k] = v
     return out
 
 

@@ -10,6 +10,9 @@ Cases (synthetic inputs from `synth`):
   fused-deep         qts_batched_fwd_bwd, one request shaped like the heaviest member of the
                      64-ensemble batch (depth 14, F = 57), 60 trees, M = 4,096
   adjoint-deep       qts_shap_backward on the same
+  interactions3-500  qts_shap_interactions3 (third order) on the 500-tree depth-6 ensemble
+  forward-adultlike  qts_shap_values on a Table-1-shaped stand-in for the paper's Adult-large
+                     model (1,000 trees, depth 16, F = 14, ~610 leaves per tree), 1,000 rows
 Prints the median CUDA-event time per call and the algorithmic FP32-pipe
 operation rate (4 ops per sample x element x node forward, 11 adjoint/fused).
 """
@@ -34,7 +37,8 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["forward-xgb", "adjoint-xgb", "interactions-500", "fused-xgb",
-                                     "fused-deep", "adjoint-deep"])
+                                     "fused-deep", "adjoint-deep", "interactions3-500",
+                                     "forward-adultlike"])
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     if args.case.endswith("-deep"):
@@ -46,8 +50,13 @@ def main():
         ens = synth.grow(es, 60, int(depth[e]), F, int(min(100000, 20 * 2 ** int(depth[e]))), 0.1, min_rows=5)
         w = synth.Workload("deep", ens, synth.normal(es, synth.STREAM_X, (4096, F)),
                            synth.normal(es, synth.STREAM_GRAD, (4096, F + 1)))
+    elif args.case == "forward-adultlike":
+        seed = synth.SEED_BASE + 100
+        ens = synth.grow(seed, 1000, 16, 14, 1850, 0.1, min_rows=5)
+        w = synth.Workload("adultlike", ens, synth.normal(seed, synth.STREAM_X, (1000, 14)),
+                           synth.normal(seed, synth.STREAM_GRAD, (1000, 15)))
     else:
-        cfg = 3 if args.case == "interactions-500" else 1
+        cfg = 3 if args.case.startswith("interactions") else 1
         w = synth.single_config(cfg, with_grad=True)
     E = qts.Ensemble.from_arrays(w.ens)
     info = E.info()
@@ -64,6 +73,8 @@ def main():
         "fused-xgb": (lambda: qts.batched_fwd_bwd(reqs, 8), 11),
         "fused-deep": (lambda: qts.batched_fwd_bwd(reqs, 8), 11),
         "adjoint-deep": (lambda: qts.shap_backward(E, X, G, 8), 11),
+        "interactions3-500": (lambda: qts.shap_interactions3(E, X, 8), 0),
+        "forward-adultlike": (lambda: qts.shap_values(E, X, 8, out=phi), 4),
     }[args.case]
     fn()
     torch.cuda.synchronize()

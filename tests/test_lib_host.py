@@ -110,3 +110,11 @@ def test_describe_rejects_paths_beyond_64_unique_features():
     with pytest.raises(qts.QtsError) as e:
         qts.describe(ens)
     assert e.value.status == 4
+
+
+def test_triple_index_is_the_lexicographic_rank():
+    """The compact third-order layout enumerates a < b < c in lexicographic order."""
+    for F in (3, 4, 7, 12):
+        idx = qts.triple_index(F)
+        lex = [(a, b, c) for a in range(F) for b in range(a + 1, F) for c in range(b + 1, F)]
+        assert [idx[t] for t in lex] == list(range(len(lex)))

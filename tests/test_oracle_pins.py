@@ -66,6 +66,10 @@ def test_golden_hand_trees():
             for got in (bf_sii[0, 1], sii[0, 0, 1], a2[0, 1]):
                 assert abs(got - s["sii01"]) < 1e-15, (spec["name"], got)
             assert abs(oracle.predict(ens, x[None])[0] - s["fx"]) == 0
+            if "sii012" in s:
+                for got in (oracle.brute_force3(ens, x)[0, 1, 2], oracle.sii3_exact(ens, x[None])[0, 0, 1, 2],
+                            oracle.alg1(ens, x, 3, 8)[2, 0, 1]):
+                    assert abs(got - s["sii012"]) < 1e-15, (spec["name"], got)
 
 
 def test_stump_closed_form():
@@ -285,3 +289,31 @@ def test_threads_do_not_change_results():
     a = oracle.shap_exact(w.ens, w.X, n_threads=1)
     b = oracle.shap_exact(w.ens, w.X, n_threads=7)
     assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------ third order
+
+@pytest.mark.parametrize("seed", range(6))
+def test_third_order_exact_equals_brute_force(seed):
+    """Thm 1 with |S| = 3 integrated exactly == subset enumeration with the
+    order-3 Shapley interaction weights (App. C), repeated features included."""
+    ens = tiny_ensemble(1600 + seed, n_trees=3, depth=8, F=6)
+    X = synth.normal(1600 + seed, 1, (3, 6))
+    s3 = oracle.sii3_exact(ens, X)
+    for s in range(3):
+        bf = oracle.brute_force3(ens, X[s])
+        assert np.abs(s3[s] - bf).max() < 1e-12 * max(1.0, np.abs(bf).max())
+        assert np.allclose(bf, np.transpose(bf, (1, 0, 2)), atol=0)
+        assert np.allclose(bf, np.transpose(bf, (0, 2, 1)), atol=0)
+
+
+def test_third_order_alg1_exact_at_theorem2_bound():
+    """Algorithm 1 with s = 3 and n = ceil((d - 2)/2) points is exact (Thm 2)."""
+    ens = tiny_ensemble(1700, n_trees=3, depth=10, F=9, n_train=3000)
+    _, dmax, _ = oracle.path_stats(ens)
+    X = synth.normal(1700, 1, (2, 9))
+    n = math.ceil((dmax - 3 + 1) / 2)
+    ref = oracle.sii3_exact(ens, X)
+    for s in range(2):
+        got = oracle.alg1(ens, X[s], 3, n)
+        assert np.abs(got - ref[s]).max() < 1e-12 * max(1.0, np.abs(ref[s]).max())
