@@ -26,13 +26,21 @@ struct SegDev {
     int32_t paths;      // paths per item
     int32_t n_tiles;    // sample groups per chunk (a group = 32, or 32 per warp when priv)
     int32_t req;
-    int32_t priv;       // 1: each warp owns 32 samples and a private phi tile
+    int32_t priv;       // 0: warps share 32 samples (atomics); 1: each warp owns 32
+                        // samples and a private phi tile; 2: each warp owns 64
+                        // samples, two per lane (sample-pair packing), private tile
     int32_t pad;
 };
 
 // Requests with F + 1 <= kPrivRows use per-warp private phi tiles (plain
 // read-add-write); wider ones share one tile with shared-memory atomics.
 constexpr int kPrivRows = 64;
+// Widths that run the fused pass with sample-pair packing when the 64-sample
+// tile fits the class's shared memory.  Widths 7-8 and 11-12 sit at the top of
+// their register classes (caps 128 and 168) and spill when packed, so they keep
+// one sample per lane; class 12 with widths 9-10 packed spills 24 bytes a thread
+// and still measured faster than unpacked.
+__host__ __device__ constexpr bool pair_width(int D) { return D <= 6 || (D >= 9 && D <= 10) || (D >= 13 && D <= 16); }
 constexpr int kBatchWarps = 4;
 
 // Per request: x and grad_phi transposed to [feature][Mpad] (row F of XT is
@@ -56,13 +64,24 @@ struct BatchArgs {
     const ReqDev* reqs;
     int64_t n_items;
     unsigned long long* counter;
-    int tile_rows;      // rows of the phi region (max of shared and private needs)
+    int64_t tile_floats;  // floats of the phi region (max over the launch's requests)
     int sub;
     QuadF q;
 };
 
-size_t batch_smem_bytes(int rows, int sub, int dmax) {
-    size_t off = (size_t)rows * kTileLd * 4;
+// samples per item for each mode
+__host__ __device__ __forceinline__ int item_samples(int priv) {
+    return priv == 2 ? 64 * kBatchWarps : (priv == 1 ? 32 * kBatchWarps : 32);
+}
+
+// floats of the phi region a request needs in a mode
+inline int64_t tile_floats_for(int priv, int F) {
+    return priv == 2 ? (int64_t)kBatchWarps * (F + 1) * kTileLd2
+                     : (priv == 1 ? (int64_t)kBatchWarps * (F + 1) * kTileLd : (int64_t)(F + 1) * kTileLd);
+}
+
+size_t batch_smem_bytes(int64_t tile_floats, int sub, int dmax) {
+    size_t off = (size_t)tile_floats * 4;
     off = (off + 15) & ~(size_t)15;
     off += 2 * (size_t)sub * (dmax + 1) * sizeof(Rec32);
     off = (off + 15) & ~(size_t)15;
@@ -106,9 +125,45 @@ __global__ void transpose_pad_kernel(const float* __restrict__ in, int64_t M, in
 template <int D>
 __device__ __forceinline__ bool batch_item(const SegDev& sg, const ReqDev& rq, int64_t p0, int64_t p1,
                                            int64_t s0, float* ps, Rec32* st0, Rec32* st1, uint64_t* bars,
-                                           uint32_t* s_phase, int* s_flag, int sub, const QuadF& q) {
+                                           uint32_t* s_phase, int* s_flag, int sub, const QuadF& q,
+                                           float2* zs_all) {
     const int F = rq.F;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if constexpr (pair_width(D)) {
+        if (sg.priv == 2) {
+            // sample-pair mode: warp w owns samples s0 + 64 w .. + 63, lane l the pair 2l, 2l+1
+            const int tile_elems = (F + 1) * kTileLd2;
+            float* my = ps + warp * tile_elems;
+            float2* zs = zs_all + warp * 16;
+            const int64_t sw = s0 + 64 * warp;
+            for (int idx = lane; idx < tile_elems; idx += 32) my[idx] = 0.f;
+            __syncthreads();
+            const bool has_nan = *rq.has_nan != 0;
+            const GlobalCols2 xr{rq.XT, rq.Mpad, sw + 2 * lane};
+            const GlobalCols2 gr{rq.GT, rq.Mpad, sw + 2 * lane};
+            const bool ok = stream_paths<Rec32, D>(
+                sg.rec, p0, p1, sub, st0, st1, bars, s_phase, s_flag, rq.status,
+                [&](int64_t p, const Rec32* r) {
+                    double* gsl = sg.g_slot + p * D;
+                    double* gv = sg.g_val + p;
+                    if (has_nan) bwd_path_f32_sp<D, true>(r, xr, gr, my, zs, lane, q, gsl, gv);
+                    else bwd_path_f32_sp<D, false>(r, xr, gr, my, zs, lane, q, gsl, gv);
+                },
+                true);
+            if (!ok) return false;
+            if (rq.phi) {
+                for (int idx = lane; idx < 64 * F; idx += 32) {
+                    const int s = idx / F, f = idx - s * F;
+                    if (sw + s < rq.M) {
+                        const float v = my[f * kTileLd2 + s];
+                        if (v != 0.f) atomicAdd(&rq.phi[(sw + s) * (F + 1) + f], (double)v);
+                    }
+                }
+            }
+            __syncthreads();
+            return true;
+        }
+    }
     const bool priv = sg.priv != 0;
     const int tile_elems = (F + 1) * kTileLd;
     // private mode: warp w owns samples s0 + 32 w .. and tile w
@@ -180,15 +235,15 @@ template <int DCLASS>
 __global__ void __launch_bounds__(128, DCLASS == 8 ? 4 : (DCLASS == 12 ? 3 : (DCLASS == 16 ? 2 : 1)))
     batch_kernel(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const size_t rows = a.tile_rows;
     float* ps = (float*)smem;
-    size_t off = (rows * kTileLd * 4 + 15) & ~(size_t)15;
+    size_t off = ((size_t)a.tile_floats * 4 + 15) & ~(size_t)15;
     Rec32* st0 = (Rec32*)(smem + off);
     Rec32* st1 = st0 + (size_t)a.sub * (DCLASS + 1);
     uint64_t* bars = (uint64_t*)(st1 + (size_t)a.sub * (DCLASS + 1));
     __shared__ int s_flag;
     __shared__ uint32_t s_phase[2];
     __shared__ long long s_item;
+    __shared__ float2 s_zs[kBatchWarps * 16];
     if (threadIdx.x == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -211,12 +266,12 @@ __global__ void __launch_bounds__(128, DCLASS == 8 ? 4 : (DCLASS == 12 ? 3 : (DC
         const SegDev sg = a.segs[lo];
         const ReqDev rq = a.reqs[sg.req];
         const int64_t local = item - sg.item_begin;
-        const int64_t s0 = (local % sg.n_tiles) * (sg.priv ? 32 * kBatchWarps : 32);
+        const int64_t s0 = (local % sg.n_tiles) * item_samples(sg.priv);
         const int64_t p0 = (local / sg.n_tiles) * sg.paths;
         const int64_t p1 = imin64(p0 + sg.paths, sg.n_paths);
         bool ok = true;
 #define QTS_CASE(DD) \
-    case DD: ok = batch_item<DD>(sg, rq, p0, p1, s0, ps, st0, st1, bars, s_phase, &s_flag, a.sub, a.q); break;
+    case DD: ok = batch_item<DD>(sg, rq, p0, p1, s0, ps, st0, st1, bars, s_phase, &s_flag, a.sub, a.q, s_zs); break;
         if constexpr (DCLASS == 8) {
             switch (sg.D) {
                 QTS_CASE(1) QTS_CASE(2) QTS_CASE(3) QTS_CASE(4) QTS_CASE(5) QTS_CASE(6)
@@ -293,6 +348,13 @@ void batch_forget(const qts_ensemble* e) {
 }
 
 int batch_class(int D) { return D <= 8 ? 8 : D <= 12 ? 12 : (D <= 16 ? 16 : (D <= 32 ? 32 : 64)); }
+static int class_index(int cls) { return cls == 8 ? 0 : cls == 12 ? 1 : cls == 16 ? 2 : cls == 32 ? 3 : 4; }
+// shared memory one block of a class may use and still reach its blocks per SM
+static size_t class_smem_budget(int cls) {
+    const size_t sm = 227 * 1024;
+    const int blocks = cls == 8 ? 4 : cls == 12 ? 3 : cls == 16 ? 2 : 1;
+    return sm / blocks - 1024;
+}
 
 template <int C>
 static cudaError_t launch_batch_class(const BatchArgs& a, size_t smem, cudaStream_t st, int* blocks_out) {
@@ -330,7 +392,7 @@ static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 static BatchWork batch_work(const qts_ensemble* e, int64_t M, int F, bool grad) {
     BatchWork w;
-    w.Mpad = (M + 32 * kBatchWarps - 1) / (32 * kBatchWarps) * (32 * kBatchWarps);
+    w.Mpad = (M + 64 * kBatchWarps - 1) / (64 * kBatchWarps) * (64 * kBatchWarps);
     w.grad_bytes = grad ? align256(sizeof(double) * (size_t)(4 + e->prep.n_paths + e->prep.n_slots)) : 0;
     const size_t tbytes = align256(sizeof(float) * (size_t)(F + 1) * (size_t)w.Mpad);
     w.xt_off = w.grad_bytes;
@@ -357,7 +419,8 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
     };
     std::vector<SegHost> segs;
     std::vector<ReqDev> rd(n);
-    int Fmax = 1, Fpriv = 0;
+    int64_t tile_need[5] = {0, 0, 0, 0, 0};  // per register class index
+    const int sub = 32;                        // paths per staged sub-chunk
     for (int r = 0; r < n; ++r) {
         const qts_request& R = reqs[r];
         qts_ensemble* e = R.ens;
@@ -366,14 +429,18 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
         char* wbase = (char*)e->d_work;
         rd[r] = {(const float*)(wbase + bw.xt_off), grad ? (const float*)(wbase + bw.gt_off) : nullptr, R.phi,
                  R.M, bw.Mpad, R.F, 0, (const int*)(wbase + bw.flag_off), e->d_status};
-        const bool priv = R.F + 1 <= kPrivRows;
-        if (priv) Fpriv = std::max(Fpriv, R.F);
-        else Fmax = std::max(Fmax, R.F);
         if (R.M <= 0) continue;
         double* g_val = grad ? (double*)e->d_work + 4 : nullptr;
         double* g_slot = grad ? g_val + e->prep.n_paths : nullptr;
-        const int n_tiles = (int)(priv ? (R.M + 32 * kBatchWarps - 1) / (32 * kBatchWarps) : (R.M + 31) / 32);
         for (const Bucket& b : e->prep.buckets) {
+            const int cls = batch_class(b.D), ci = class_index(cls);
+            int mode = R.F + 1 <= kPrivRows ? 1 : 0;
+            if (grad && pair_width(b.D) &&
+                batch_smem_bytes(tile_floats_for(2, R.F), sub, cls) <= class_smem_budget(cls))
+                mode = 2;
+            tile_need[ci] = std::max(tile_need[ci], tile_floats_for(mode, R.F));
+            const int per_item = item_samples(mode);
+            const int n_tiles = (int)((R.M + per_item - 1) / per_item);
             SegHost s;
             s.d.rec = (const Rec32*)e->d_rec + b.rec_off;
             s.d.g_val = grad ? g_val + b.path_base : nullptr;
@@ -383,10 +450,10 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
             s.d.paths = e->tuned ? e->tune[b.D].bpaths : item_paths(b.D, grad);
             s.d.n_tiles = n_tiles;
             s.d.req = r;
-            s.d.priv = priv ? 1 : 0;
+            s.d.priv = mode;
             s.d.pad = 0;
             s.cost = (double)s.d.paths * b.D * (grad ? 12 : 4);
-            s.cls = batch_class(b.D);
+            s.cls = cls;
             segs.push_back(s);
         }
     }
@@ -395,7 +462,6 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
         if (a.cls != b.cls) return a.cls < b.cls;
         return a.cost > b.cost;
     });
-    const int sub = 32;
     std::vector<int> cls_list;
     std::vector<int64_t> cls_items, cls_first_seg;
     int64_t item = 0;
@@ -465,10 +531,10 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
         a.reqs = d_reqs;
         a.n_items = cls_items[c];
         a.counter = d_cnt + c;
-        a.tile_rows = std::max(Fmax + 1, Fpriv > 0 ? kBatchWarps * (Fpriv + 1) : 0);
+        a.tile_floats = std::max<int64_t>(tile_need[class_index(cls)], kTileLd);
         a.sub = sub;
         a.q = q;
-        const size_t smem = batch_smem_bytes(a.tile_rows, sub, cls);
+        const size_t smem = batch_smem_bytes(a.tile_floats, sub, cls);
         int blocks = 0;
         if (cls == 8) err = launch_batch_class<8>(a, smem, cap, &blocks);
         else if (cls == 12) err = launch_batch_class<12>(a, smem, cap, &blocks);

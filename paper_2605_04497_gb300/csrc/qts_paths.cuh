@@ -355,6 +355,93 @@ __device__ __forceinline__ void bwd_path_f32_pk(const Rec32* __restrict__ r, con
     flush_path_grads<D, float>(dz, dval, lane, g_slot_p, g_val_p);
 }
 
+// ------------------------------------------------- two samples per lane --
+//
+// Sample-pair packing: lane l handles samples 2l and 2l+1 of a 64-sample tile
+// and every f32x2 operation covers the two samples at one quadrature node, so
+// (o - z) and g (o - z) are natural pairs, the node sums need no horizontal
+// adds, and the per-path setup and warp reduction serve 64 samples.
+// {z_j, z_j} pairs come from this warp's shared scratch zs[0..D).
+// The private phi tile has rows of kTileLd2 floats (lane l owns columns 2l, 2l+1).
+constexpr int kTileLd2 = 66;
+
+// 64-bit shared load that the compiler may not hoist out of the node loop
+// (keeping all D pairs live would cost 2 D registers).
+__device__ __forceinline__ float2 lds_pair(const float2* p) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(smem_u32(p)));
+    return v;
+}
+
+struct GlobalCols2 {  // transposed global copy [feature][ld]; samples s, s+1 (s even)
+    const float* t;
+    int64_t ld;
+    int64_t s;
+    __device__ __forceinline__ float2 operator()(int f) const {
+        return __ldg(reinterpret_cast<const float2*>(t + (int64_t)f * ld + s));
+    }
+};
+
+template <int D, bool HAS_NAN>
+__device__ __forceinline__ void bwd_path_f32_sp(const Rec32* __restrict__ r, const GlobalCols2& xr,
+                                                const GlobalCols2& gr, float* ps, float2* zs, int lane,
+                                                const QuadF& q, double* g_slot_p, double* g_val_p) {
+    const float val = r[0].z;
+    float2 d2[D], u2[D], a1[D], a2[D];
+    __syncwarp();
+    if (lane < D) zs[lane] = f2s(r[1 + lane].z);
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const Rec32 e = r[1 + j];
+        const int f = feat_of(e.bits);
+        const float2 x = xr(f);
+        const bool oa = satisfies<HAS_NAN>(x.x, e.lo, e.hi, e.bits);
+        const bool ob = satisfies<HAS_NAN>(x.y, e.lo, e.hi, e.bits);
+        d2[j] = f2((oa ? 1.f : 0.f) - e.z, (ob ? 1.f : 0.f) - e.z);
+        u2[j] = mul2(gr(f), d2[j]);
+        a1[j] = f2s(0.f);
+        a2[j] = f2s(0.f);
+    }
+    __syncwarp();
+    for (int m = 0; m < q.n_pad; ++m) {
+        const float2 T = f2s(q.t[m]);
+        const float2 C2 = f2s(1.f - q.t[m]);
+        float2 P[D], PU[D];
+        P[0] = f2s(q.w[m]);
+        PU[0] = f2s(0.f);
+#pragma unroll
+        for (int j = 0; j + 1 < D; ++j) {
+            const float2 a = fma2(T, d2[j], lds_pair(zs + j));
+            P[j + 1] = mul2(P[j], a);
+            PU[j + 1] = fma2(PU[j], a, mul2(u2[j], P[j]));
+        }
+        float2 S = f2s(1.f), SU = f2s(0.f);
+#pragma unroll
+        for (int j = D - 1; j >= 0; --j) {
+            a1[j] = fma2(P[j], S, a1[j]);
+            a2[j] = fma2(C2, fma2(P[j], SU, mul2(PU[j], S)), a2[j]);
+            if (j > 0) {
+                const float2 a = fma2(T, d2[j], lds_pair(zs + j));
+                SU = fma2(SU, a, mul2(u2[j], S));
+                S = mul2(S, a);
+            }
+        }
+    }
+    float2 dval2 = f2s(0.f);
+    float dz[D];
+    const float2 v2 = f2s(val);
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const int f = feat_of(r[1 + j].bits);
+        dval2 = fma2(u2[j], a1[j], dval2);
+        const float2 dzj = mul2(v2, fma2(f2s(-1.f), mul2(gr(f), a1[j]), a2[j]));
+        dz[j] = dzj.x + dzj.y;
+        float2* cell = reinterpret_cast<float2*>(ps + f * kTileLd2 + 2 * lane);
+        *cell = fma2(mul2(v2, d2[j]), a1[j], *cell);  // private tile: plain read-add-write
+    }
+    flush_path_grads<D, float>(dz, dval2.x + dval2.y, lane, g_slot_p, g_val_p);
+}
+
 // ------------------------------------------------------------------ FP64 --
 
 template <int D, bool HAS_NAN>
