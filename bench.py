@@ -33,12 +33,13 @@ UNIT = "sample·trees/s"
 WORKLOAD = ("batch64: 64 ensembles, trees log-U[10,2000], depth U{3..16}, F log-U[8,200], "
             "M log-U[1,50000], covers from min(100000, 20*2^depth) rows, grad_phi ~N(0,1), seed 20260504")
 N_QUAD = 8
-# DRAM bytes (read + write) of the three persistent launches of one step, from
-# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:batch_kernel -c 3`
-# on this benchmark (profiles/batch_kernel_dram_batch64.md); valid only while the
-# kernel sources hash to KERNEL_HASH, otherwise reported as null.
-TRAFFIC_BYTES = (6.80 + 2.93 + 11.90 + 4.07 + 6.44 + 2.15) * 1e9
-TRAFFIC_HASH = "15e45ed45a795985"
+# DRAM bytes (read + write) of the three persistent launches of one step: the
+# mean over the three graph runs of `ncu --metrics gpu__time_duration.sum,
+# dram__bytes_read.sum,dram__bytes_write.sum` on `bench.py --steps 1 --warmup 1`
+# (profiles/batch_kernel_dram_batch64.md); valid only while the kernel sources
+# hash to TRAFFIC_HASH, otherwise reported as null.
+TRAFFIC_BYTES = (1.682 + 0.799 + 12.481 + 4.918 + 11.352 + 3.829) * 1e9
+TRAFFIC_HASH = "639d17067e223692"
 KERNEL_SOURCES = ("qts_batch.cu", "qts_paths.cuh", "qts_device.cuh", "qts_internal.h")
 # FP32-pipe operations per (sample, merged path element, quadrature node)
 OPS_FUSED = 11   # forward + adjoint in one pass

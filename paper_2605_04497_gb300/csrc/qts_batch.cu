@@ -36,11 +36,9 @@ struct SegDev {
 // read-add-write); wider ones share one tile with shared-memory atomics.
 constexpr int kPrivRows = 64;
 // Widths that run the fused pass with sample-pair packing when the 64-sample
-// tile fits the class's shared memory.  Widths 7-8 and 11-12 sit at the top of
-// their register classes (caps 128 and 168) and spill when packed, so they keep
-// one sample per lane; class 12 with widths 9-10 packed spills 24 bytes a thread
-// and still measured faster than unpacked.
-__host__ __device__ constexpr bool pair_width(int D) { return D <= 6 || (D >= 9 && D <= 10) || (D >= 13 && D <= 16); }
+// tile fits the class's shared memory.  The register classes below are cut so
+// that every packed width fits its class's cap without spilling.
+__host__ __device__ constexpr bool pair_width(int D) { return D <= 16; }
 constexpr int kBatchWarps = 4;
 
 // Per request: x and grad_phi transposed to [feature][Mpad] (row F of XT is
@@ -228,9 +226,11 @@ __device__ __forceinline__ bool batch_item(const SegDev& sg, const ReqDev& rq, i
     return true;
 }
 
-// Register classes: DCLASS 8 handles widths 1..8 (4 blocks of 128 threads per
-// SM), 12 handles 9..12 (3 blocks), 16 handles 13..16 (2 blocks), 32 handles
-// 20..32 and 64 handles 40..64.
+// Register classes: DCLASS 8 handles widths 1..6 (4 blocks of 128 threads per
+// SM, 128 registers), 12 handles 7..10 (3 blocks, 168 registers), 16 handles
+// 11..16 (2 blocks, 255 registers), 32 handles 20..32 and 64 handles 40..64.
+// With two samples per lane a width needs about as many registers as twice
+// that width with one, so the cuts sit lower than the widths' names suggest.
 template <int DCLASS>
 __global__ void __launch_bounds__(128, DCLASS == 8 ? 4 : (DCLASS == 12 ? 3 : (DCLASS == 16 ? 2 : 1)))
     batch_kernel(BatchArgs a) {
@@ -275,17 +275,16 @@ __global__ void __launch_bounds__(128, DCLASS == 8 ? 4 : (DCLASS == 12 ? 3 : (DC
         if constexpr (DCLASS == 8) {
             switch (sg.D) {
                 QTS_CASE(1) QTS_CASE(2) QTS_CASE(3) QTS_CASE(4) QTS_CASE(5) QTS_CASE(6)
-                QTS_CASE(7) QTS_CASE(8)
                 default: break;
             }
         } else if constexpr (DCLASS == 12) {
             switch (sg.D) {
-                QTS_CASE(9) QTS_CASE(10) QTS_CASE(11) QTS_CASE(12)
+                QTS_CASE(7) QTS_CASE(8) QTS_CASE(9) QTS_CASE(10)
                 default: break;
             }
         } else if constexpr (DCLASS == 16) {
             switch (sg.D) {
-                QTS_CASE(13) QTS_CASE(14) QTS_CASE(15) QTS_CASE(16)
+                QTS_CASE(11) QTS_CASE(12) QTS_CASE(13) QTS_CASE(14) QTS_CASE(15) QTS_CASE(16)
                 default: break;
             }
         } else if constexpr (DCLASS == 32) {
@@ -347,7 +346,7 @@ void batch_forget(const qts_ensemble* e) {
     }
 }
 
-int batch_class(int D) { return D <= 8 ? 8 : D <= 12 ? 12 : (D <= 16 ? 16 : (D <= 32 ? 32 : 64)); }
+int batch_class(int D) { return D <= 6 ? 8 : D <= 10 ? 12 : (D <= 16 ? 16 : (D <= 32 ? 32 : 64)); }
 static int class_index(int cls) { return cls == 8 ? 0 : cls == 12 ? 1 : cls == 16 ? 2 : cls == 32 ? 3 : 4; }
 // shared memory one block of a class may use and still reach its blocks per SM
 static size_t class_smem_budget(int cls) {
