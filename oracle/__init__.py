@@ -69,9 +69,10 @@ def _load():
         lib.orc_path_stats.argtypes = [E, vp, vp, vp]
         lib.orc_sii3_exact.argtypes = [E, vp, i64, i32, vp]
         lib.orc_brute_force3.argtypes = [E, vp, vp]
+        lib.orc_alg1_shap.argtypes = [E, vp, i64, i32, i32, vp]
         for f in ("orc_gl_nodes", "orc_shap_exact", "orc_sii_exact", "orc_shap_quad",
                   "orc_brute_force", "orc_alg1", "orc_grad_exact", "orc_path_stats",
-                  "orc_sii3_exact", "orc_brute_force3"):
+                  "orc_sii3_exact", "orc_brute_force3", "orc_alg1_shap"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -210,6 +211,17 @@ def alg1(ens, x, order: int, n: int) -> np.ndarray:
     out = np.zeros(b.F + 1 if order == 1 else ((b.F, b.F) if order == 2 else (b.F, b.F, b.F)))
     _check(_load().orc_alg1(b.ref(), x.ctypes.data, order, n, out.ctypes.data), "orc_alg1")
     return out
+
+
+def alg1_shap(ens, X, n: int = 8, n_threads: int | None = None) -> np.ndarray:
+    """phi (M x (F+1)) by Algorithm 1 with n Gauss-Legendre points, threaded over
+    samples; at most min(n_threads, M) threads run."""
+    b = _Bound(ens)
+    X = _f32(X, b.F)
+    phi = np.zeros((X.shape[0], b.F + 1))
+    _check(_load().orc_alg1_shap(b.ref(), X.ctypes.data, X.shape[0], n, n_threads or threads(),
+                                 phi.ctypes.data), "orc_alg1_shap")
+    return phi
 
 
 def grad_exact(ens, X, grad_phi, leaves=None, n_threads: int | None = None):

@@ -700,6 +700,56 @@ int orc_alg1(const orc_ens *e, const float *x, int order, int n, double *out) {
     return 0;
 }
 
+/* Algorithm 1 as a CPU quadrature method: first-order phi for M samples with
+ * n Gauss-Legendre points, threads over samples (each thread runs the DFS of
+ * orc_alg1 on its rows).  This is the paper's own CPU formulation (Sec. 5,
+ * Algorithm 1), not the exact expansion. */
+typedef struct {
+    const orc_ens *e;
+    const float *X;
+    int64_t s_begin, s_end;
+    int n;
+    double *phi;
+    int rc;
+} a1job_t;
+
+static void *alg1_shap_worker(void *arg) {
+    a1job_t *J = (a1job_t *)arg;
+    const int F = J->e->n_features;
+    for (int64_t s = J->s_begin; s < J->s_end; ++s)
+        if (orc_alg1(J->e, J->X + s * F, 1, J->n, J->phi + s * (F + 1)) != 0) J->rc = -1;
+    return NULL;
+}
+
+int orc_alg1_shap(const orc_ens *e, const float *X, int64_t M, int n, int n_threads, double *phi) {
+    if (M < 0 || n < 1 || n > 256) return -1;
+    if (M == 0) return 0;
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > M) n_threads = (int)M;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
+    a1job_t *jobs = (a1job_t *)malloc(sizeof(a1job_t) * (size_t)n_threads);
+    if (!th || !jobs) { free(th); free(jobs); return -1; }
+    int64_t per = (M + n_threads - 1) / n_threads;
+    for (int i = 0; i < n_threads; ++i) {
+        jobs[i].e = e;
+        jobs[i].X = X;
+        jobs[i].n = n;
+        jobs[i].phi = phi;
+        jobs[i].rc = 0;
+        jobs[i].s_begin = i * per < M ? i * per : M;
+        jobs[i].s_end = (i + 1) * per < M ? (i + 1) * per : M;
+        pthread_create(&th[i], NULL, alg1_shap_worker, &jobs[i]);
+    }
+    int rc = 0;
+    for (int i = 0; i < n_threads; ++i) {
+        pthread_join(th[i], NULL);
+        if (jobs[i].rc) rc = -1;
+    }
+    free(th);
+    free(jobs);
+    return rc;
+}
+
 /* ========================================================= gradients ===== */
 
 /* L = sum_s sum_i g_{s,f_i} phi_{s,f_i} + sum_s grad_phi[s,F] E[f], with

@@ -17,6 +17,7 @@
  *                       Path-Dependent game (Eq. path_dependent_game, App. C).
  *   orc_brute_force3    SII_ijk by subset enumeration.
  *   orc_alg1            Algorithm 1 (DFS with telescoping, orders 1, 2 and 3).
+ *   orc_alg1_shap       Algorithm 1, first order, many samples on threads.
  *   orc_grad_exact      d(sum grad_phi*phi)/d(leaf values) and /d(edge weights),
  *                       differentiating Thm 1 analytically (no paper passage;
  *                       pinned by finite differences of the brute force).
@@ -76,6 +77,10 @@ int orc_brute_force3(const orc_ens *e, const float *x, double *sii3);
  * (F+1 incl. E[f]), order 2 fills sii (F x F, symmetric, zero diagonal),
  * order 3 fills F x F x F (symmetric, zero where indices coincide). */
 int orc_alg1(const orc_ens *e, const float *x, int order, int n, double *out);
+
+/* Algorithm 1, first order, for M samples (phi: M x (F+1) incl. E[f]),
+ * threaded over samples: the paper's CPU quadrature method as a baseline. */
+int orc_alg1_shap(const orc_ens *e, const float *X, int64_t M, int n, int n_threads, double *phi);
 
 /* L = sum_s sum_{f<=F} grad_phi[s,f] * phi[s,f].  Writes dL/d leaf_value and
  * dL/d z for every node (N = node_offsets[n_trees]).  If leaves != NULL only

@@ -215,6 +215,21 @@ def test_alg1_exact_at_theorem2_bound(order):
         assert np.abs(got - ref).max() < 1e-12 * scale
 
 
+def test_alg1_threaded_equals_single_sample_dfs_and_exact():
+    """The threaded Algorithm 1 runs the same DFS per row (bit-identical to
+    the single-sample call, whatever the thread count) and, with 8 points on
+    paths of at most 16 unique features, equals the exact expansion (Thm 2)."""
+    sub = synth.single_config(1, n_samples=9, n_trees=12)
+    a = oracle.alg1_shap(sub.ens, sub.X, 8, n_threads=4)
+    b = oracle.alg1_shap(sub.ens, sub.X, 8, n_threads=1)
+    assert np.array_equal(a, b)
+    for s in range(sub.X.shape[0]):
+        assert np.array_equal(a[s], oracle.alg1(sub.ens, sub.X[s], 1, 8))
+    ref = oracle.shap_exact(sub.ens, sub.X)
+    assert rel_err_rows(a, ref).max() < 1e-12
+    assert oracle.alg1_shap(sub.ens, sub.X[:0], 8).shape == (0, sub.F + 1)
+
+
 def test_quadrature_exact_iff_degree_covered():
     """n-point quadrature equals the exact integral for paths with d <= 2n
     unique features (integrand degree d - 1 <= 2n - 1), and misses it once d
