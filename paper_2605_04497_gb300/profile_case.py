@@ -13,6 +13,8 @@ Cases (synthetic inputs from `synth`):
   interactions3-500  qts_shap_interactions3 (third order) on the 500-tree depth-6 ensemble
   forward-adultlike  qts_shap_values on a Table-1-shaped stand-in for the paper's Adult-large
                      model (1,000 trees, depth 16, F = 14, ~610 leaves per tree), 1,000 rows
+  forward-deep20     qts_shap_values on 200 unbalanced trees of depth <= 20 over F = 24
+                     (repeated features merged), M = 5,000
 Prints the median CUDA-event time per call and the algorithmic FP32-pipe
 operation rate (4 ops per sample x element x node forward, 11 adjoint/fused).
 """
@@ -38,7 +40,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["forward-xgb", "adjoint-xgb", "interactions-500", "fused-xgb",
                                      "fused-deep", "adjoint-deep", "interactions3-500",
-                                     "forward-adultlike"])
+                                     "forward-adultlike", "forward-deep20"])
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     if args.case.endswith("-deep"):
@@ -55,9 +57,11 @@ def main():
         ens = synth.grow(seed, 1000, 16, 14, 1850, 0.1, min_rows=5)
         w = synth.Workload("adultlike", ens, synth.normal(seed, synth.STREAM_X, (1000, 14)),
                            synth.normal(seed, synth.STREAM_GRAD, (1000, 15)))
+    elif args.case == "forward-deep20":
+        w = synth.workload("deep-depth20", with_grad=True)
     else:
-        cfg = 3 if args.case.startswith("interactions") else 1
-        w = synth.single_config(cfg, with_grad=True)
+        w = synth.workload("pairs-depth6" if args.case.startswith("interactions") else "xgb-depth8",
+                           with_grad=True)
     E = qts.Ensemble.from_arrays(w.ens)
     info = E.info()
     X = torch.from_numpy(w.X).cuda()
@@ -75,6 +79,7 @@ def main():
         "adjoint-deep": (lambda: qts.shap_backward(E, X, G, 8), 11),
         "interactions3-500": (lambda: qts.shap_interactions3(E, X, 8), 0),
         "forward-adultlike": (lambda: qts.shap_values(E, X, 8, out=phi), 4),
+        "forward-deep20": (lambda: qts.shap_values(E, X, 8, out=phi), 4),
     }[args.case]
     fn()
     torch.cuda.synchronize()

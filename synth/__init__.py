@@ -189,15 +189,21 @@ def batch_draw(seed: int, n_ens: int = 64, trees=(10, 2000), depth=(3, 16), feat
 
 # --------------------------------------------------------------- workloads ---
 
-CONFIGS = {
-    0: dict(n_trees=10, max_depth=4, n_features=8, n_samples=100, n_train=1000, leaf_std=1.0,
-            full_depth=True),
-    1: dict(n_trees=1000, max_depth=8, n_features=50, n_samples=10000, n_train=100000,
-            leaf_std=0.1, full_depth=False),
-    2: dict(n_trees=200, max_depth=20, n_features=24, n_samples=5000, n_train=200000,
-            leaf_std=0.1, full_depth=False),
-    3: dict(n_trees=500, max_depth=6, n_features=30, n_samples=2000, n_train=50000,
-            leaf_std=0.1, full_depth=False),
+# The fixed workloads, by name: (seed offset, shape).  The seed of each is
+# SEED_BASE + its offset.
+WORKLOADS = {
+    # 10 trees grown to full depth 4, F = 8, M = 100: the small parity case
+    "small-depth4": (0, dict(n_trees=10, max_depth=4, n_features=8, n_samples=100, n_train=1000,
+                             leaf_std=1.0, full_depth=True)),
+    # XGBoost-shaped: 1,000 trees of depth <= 8, F = 50, M = 10,000
+    "xgb-depth8": (1, dict(n_trees=1000, max_depth=8, n_features=50, n_samples=10000, n_train=100000,
+                           leaf_std=0.1, full_depth=False)),
+    # deep unbalanced trees: 200 trees of depth <= 20 over F = 24 (repeated features), M = 5,000
+    "deep-depth20": (2, dict(n_trees=200, max_depth=20, n_features=24, n_samples=5000, n_train=200000,
+                             leaf_std=0.1, full_depth=False)),
+    # pairwise interactions: 500 trees of depth <= 6, F = 30, M = 2,000
+    "pairs-depth6": (3, dict(n_trees=500, max_depth=6, n_features=30, n_samples=2000, n_train=50000,
+                             leaf_std=0.1, full_depth=False)),
 }
 
 
@@ -221,10 +227,13 @@ class Workload:
         return self.X.shape[1]
 
 
-def single_config(idx: int, n_samples: int | None = None, n_trees: int | None = None,
-                  with_grad: bool = False) -> Workload:
-    c = dict(CONFIGS[idx])
-    seed = SEED_BASE + idx
+def workload(name: str, n_samples: int | None = None, n_trees: int | None = None,
+             with_grad: bool = False) -> Workload:
+    """One of the named fixed workloads, optionally with fewer samples or trees
+    (the first trees and rows of the full workload: same seed and streams)."""
+    off, shape = WORKLOADS[name]
+    c = dict(shape)
+    seed = SEED_BASE + off
     if n_trees is not None:
         c["n_trees"] = n_trees
     m = c["n_samples"] if n_samples is None else n_samples
@@ -232,7 +241,7 @@ def single_config(idx: int, n_samples: int | None = None, n_trees: int | None = 
                min_rows=5, full_depth=c["full_depth"])
     X = normal(seed, STREAM_X, (m, c["n_features"]))
     g = normal(seed, STREAM_GRAD, (m, c["n_features"] + 1)) if with_grad else None
-    return Workload(f"config{idx}", ens, X, g, dict(c, seed=seed, n_samples=m))
+    return Workload(name, ens, X, g, dict(c, seed=seed, n_samples=m))
 
 
 def batch_config(n_ens: int = 64, seed: int | None = None, max_samples: int | None = None,

@@ -37,3 +37,22 @@ def rel_err_rows(phi, ref):
     scale = np.maximum(fx, np.abs(ref[:, :-1]).max(axis=1))
     scale = np.maximum(scale, 1e-30)
     return np.abs(phi - ref).max(axis=1) / scale
+
+
+def leaf_unique_counts(ens):
+    """Per node: the number of distinct features split on along the root path
+    of a leaf (its merged path length d), -1 at internal nodes."""
+    out = np.full(ens.n_nodes, -1, dtype=np.int64)
+    for t in range(ens.n_trees):
+        base = int(ens.node_offsets[t])
+        stack = [(0, frozenset())]
+        while stack:
+            v, feats = stack.pop()
+            g = base + v
+            if ens.left[g] < 0:
+                out[g] = len(feats)
+                continue
+            nxt = feats | {int(ens.feature[g])}
+            stack.append((int(ens.left[g]), nxt))
+            stack.append((int(ens.right[g]), nxt))
+    return out

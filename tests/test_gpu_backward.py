@@ -46,8 +46,8 @@ def rel(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
-def test_config0_gradients(qts):
-    w = synth.single_config(0, with_grad=True)
+def test_small_depth4_gradients(qts):
+    w = synth.workload("small-depth4", with_grad=True)
     dl_ref, dz_ref = oracle.grad_exact(w.ens, w.X, w.grad_phi)
     dl, dz = gpu_grad(qts, w.ens, w.X, w.grad_phi)
     assert rel(dl, dl_ref) <= TOL32 and rel(dz, dz_ref) <= TOL32
@@ -120,12 +120,12 @@ def test_fp64_finite_differences_of_gpu_forward(qts):
         assert abs(fd - dz[n]) <= 1e-9 * max(1.0, abs(dz[n]))
 
 
-def test_config1_full_size_sampled_leaves(qts):
-    """configs[1] at full size; the oracle computes the gradient of sampled
+def test_xgb_depth8_full_size_sampled_leaves(qts):
+    """The 1,000-tree depth-8 ensemble (M = 10,000) at full size; the oracle computes the gradient of sampled
     leaves exactly (d_leaf[v] and d_z[v] only depend on v's own path)."""
     import torch
 
-    w = synth.single_config(1, with_grad=True)
+    w = synth.workload("xgb-depth8", with_grad=True)
     E = qts.Ensemble.from_arrays(w.ens)
     dl, dz = qts.shap_backward(E, torch.from_numpy(w.X).cuda(), torch.from_numpy(w.grad_phi).cuda())
     E.sync_status()
@@ -143,7 +143,7 @@ def test_config1_full_size_sampled_leaves(qts):
 def test_autograd_function(qts):
     import torch
 
-    w = synth.single_config(0, n_samples=40, with_grad=True)
+    w = synth.workload("small-depth4", n_samples=40, with_grad=True)
     E = qts.Ensemble.from_arrays(w.ens)
     lv = torch.tensor(w.ens.leaf_value, requires_grad=True)
     z = torch.tensor(w.ens.z, requires_grad=True)

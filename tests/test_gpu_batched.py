@@ -128,7 +128,7 @@ def test_batched_rejects_duplicate_ensembles(qts):
 def test_autotune_keeps_results_and_writes_cache(qts, tmp_path):
     import torch
 
-    w = synth.single_config(3, n_samples=300, n_trees=40, with_grad=True)
+    w = synth.workload("pairs-depth6", n_samples=300, n_trees=40, with_grad=True)
     E = qts.Ensemble.from_arrays(w.ens)
     X = torch.from_numpy(w.X).cuda()
     before = qts.shap_values(E, X).cpu().numpy()

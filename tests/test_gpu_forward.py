@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import golden_trees, rel_err_rows, sample_x, tiny_ensemble
+from helpers import leaf_unique_counts, golden_trees, rel_err_rows, sample_x, tiny_ensemble
 
 pytestmark = pytest.mark.gpu
 
@@ -52,16 +52,16 @@ def test_golden_trees_on_gpu(qts):
         assert np.abs(got - want).max() < 1e-6
 
 
-def test_config0_full(qts):
-    w = synth.single_config(0)  # M = 100: three full tiles and a ragged one
+def test_small_depth4_full(qts):
+    w = synth.workload("small-depth4")  # M = 100: three full tiles and a ragged one
     ref = oracle.shap_exact(w.ens, w.X)
     got = run_gpu(qts, w.ens, w.X)
     assert rel_err_rows(got, ref).max() <= TOL32
     assert np.abs(got[:, -1] - ref[:, -1]).max() < 1e-12  # bias is fp64 on both sides
 
 
-def test_config0_fp64_mode(qts):
-    w = synth.single_config(0)
+def test_small_depth4_fp64_mode(qts):
+    w = synth.workload("small-depth4")
     ref = oracle.shap_exact(w.ens, w.X)
     got = run_gpu(qts, w.ens, w.X, fp64=True)
     assert rel_err_rows(got, ref).max() <= TOL64
@@ -120,7 +120,7 @@ def test_missing_values(qts):
 def test_edge_sizes(qts):
     import torch
 
-    w = synth.single_config(0)
+    w = synth.workload("small-depth4")
     for M in (1, 31, 32, 33):
         ref = oracle.shap_exact(w.ens, w.X[:M])
         got = run_gpu(qts, w.ens, w.X[:M])
@@ -145,12 +145,12 @@ def test_single_leaf_tree_only_adds_bias(qts):
     assert np.abs(got - want).max() < 1e-6
 
 
-def test_config1_full_size_sampled_rows(qts):
-    """configs[1] at full size (1000 trees, M = 10,000) in the launch
+def test_xgb_depth8_full_size_sampled_rows(qts):
+    """The 1,000-tree depth-8 ensemble at full size (M = 10,000) in the launch
     configuration the benchmark uses; the oracle checks a sample of rows."""
     import torch
 
-    w = synth.single_config(1)
+    w = synth.workload("xgb-depth8")
     E = qts.Ensemble.from_arrays(w.ens)
     Xd = torch.from_numpy(w.X).cuda()
     phi = qts.shap_values(E, Xd).cpu().numpy()
@@ -163,12 +163,51 @@ def test_config1_full_size_sampled_rows(qts):
     E.close()
 
 
-def test_config2_deep_trees_sampled(qts):
-    """configs[2] shape (depth 20, repeated features): 8 points vs the exact
+def test_deep_depth20_error_per_path_length(qts):
+    """Deep unbalanced trees (depth 20, F = 24): the error of 8 Gauss-Legendre
+    points against the exact expansion, stated per merged path length d.  phi
+    is linear in the leaf values, so zeroing every leaf of another length
+    isolates the paths of one length.  FP64 mode matches the oracle's own
+    8-point quadrature to rounding at every length, and the exact value up to
+    d = 16 (Thm 2: the first-order integrand has degree d - 1 <= 2n - 1); FP32
+    stays within its tolerance of the exact value at every length."""
+    import torch
+
+    w = synth.workload("deep-depth20", n_samples=16, n_trees=4)
+    dl = leaf_unique_counts(w.ens)
+    X = torch.from_numpy(w.X).cuda()
+    lines = ["d  leaves  |exact|max  fp64-vs-exact  oracle8-vs-exact  fp64-vs-oracle8  fp32-vs-exact(rel)"]
+    for d in sorted(set(int(v) for v in dl[dl >= 0])):
+        e = w.ens.copy()
+        e.leaf_value[(dl >= 0) & (dl != d)] = 0.0
+        ref = oracle.shap_exact(e, w.X)
+        q8 = oracle.shap_quad(e, w.X, 8)
+        scale = max(1e-30, np.abs(ref).max())
+        errs = {}
+        for fp64 in (True, False):
+            E = qts.Ensemble.from_arrays(e, fp64=fp64)
+            errs[fp64] = qts.shap_values(E, X).cpu().numpy()
+            E.sync_status()
+            E.close()
+        e64 = np.abs(errs[True] - ref).max()
+        e64q = np.abs(errs[True] - q8).max()
+        eq = np.abs(q8 - ref).max()
+        e32 = np.abs(errs[False] - ref).max() / scale
+        lines.append(f"{d:2d} {int((dl == d).sum()):6d}  {scale:9.3e}  {e64:13.3e}  {eq:16.3e}  "
+                     f"{e64q:15.3e}  {e32:18.3e}")
+        assert e64q <= TOL64 * scale, (d, e64q, scale)
+        if d <= 16:
+            assert e64 <= TOL64 * scale, (d, e64, scale)
+        assert e32 <= TOL32, (d, e32)
+    print("\n".join(lines))
+
+
+def test_deep_depth20_sampled(qts):
+    """Deep unbalanced trees (depth 20, F = 24, repeated features): 8 points vs the exact
     expansion; paths beyond 16 unique features carry quadrature error (Thm 2)."""
     import torch
 
-    w = synth.single_config(2, n_samples=256, n_trees=20)
+    w = synth.workload("deep-depth20", n_samples=256, n_trees=20)
     E = qts.Ensemble.from_arrays(w.ens)
     phi = qts.shap_values(E, torch.from_numpy(w.X).cuda()).cpu().numpy()
     E.sync_status()

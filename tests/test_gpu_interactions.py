@@ -55,8 +55,8 @@ def check(got, ens, X):
     assert np.all(got[:, :F, F] == 0) and np.all(got[:, F, :F] == 0)
 
 
-def test_config3_small(qts):
-    w = synth.single_config(3, n_samples=70, n_trees=25)
+def test_pairs_depth6_small(qts):
+    w = synth.workload("pairs-depth6", n_samples=70, n_trees=25)
     check(gpu_int(qts, w.ens, w.X), w.ens, w.X)
 
 
@@ -83,9 +83,9 @@ def test_whole_matrix_sums_to_prediction(qts):
     assert np.abs(got.sum(axis=(1, 2)) - f).max() <= TOL32 * max(1.0, np.abs(f).max())
 
 
-def test_config3_full_size_sampled_rows(qts):
-    """configs[3] at full size (500 trees, F = 30, M = 2,000)."""
-    w = synth.single_config(3)
+def test_pairs_depth6_full_size_sampled_rows(qts):
+    """The 500-tree depth-6 interaction workload at full size (F = 30, M = 2,000)."""
+    w = synth.workload("pairs-depth6")
     got = gpu_int(qts, w.ens, w.X)
     rows = np.r_[0:6, 1000:1004, 1994:2000]
     check(got[rows], w.ens, w.X[rows])

@@ -71,7 +71,7 @@ def test_missing_values_and_ragged(qts):
 
 def test_interaction_sized_config(qts):
     """The 500-tree depth-6 F = 30 shape (subset of trees and samples)."""
-    w = synth.single_config(3, n_samples=40, n_trees=25)
+    w = synth.workload("pairs-depth6", n_samples=40, n_trees=25)
     check(gpu3(qts, w.ens, w.X), w.ens, w.X)
 
 

@@ -63,8 +63,8 @@ def test_describe_matches_oracle_paths_and_bias():
         assert abs(info["expected_value"] - phi[0, F]) < 1e-12 * max(1, abs(phi[0, F]))
 
 
-def test_describe_config1_buckets():
-    w = synth.single_config(1, n_samples=1, n_trees=50)
+def test_describe_xgb_depth8_buckets():
+    w = synth.workload("xgb-depth8", n_samples=1, n_trees=50)
     info = qts.describe(w.ens)
     widths = [d for d, _ in info["buckets"]]
     assert widths == sorted(widths) and max(widths) <= 8

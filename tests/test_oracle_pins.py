@@ -133,11 +133,11 @@ def test_null_player_and_player_count():
 
 def test_efficiency_local_accuracy():
     """sum_i phi_i + E[f] = f(x) (the paper's accuracy metric, Sec. 8)."""
-    w = synth.single_config(0)
+    w = synth.workload("small-depth4")
     phi = oracle.shap_exact(w.ens, w.X)
     f = oracle.predict(w.ens, w.X)
     assert np.abs(phi.sum(axis=1) - f).max() < 1e-12
-    sub = synth.single_config(1, n_samples=20, n_trees=20)
+    sub = synth.workload("xgb-depth8", n_samples=20, n_trees=20)
     phi = oracle.shap_exact(sub.ens, sub.X)
     f = oracle.predict(sub.ens, sub.X)
     assert np.abs(phi.sum(axis=1) - f).max() < 1e-12
@@ -187,7 +187,7 @@ def test_missing_values_follow_default_direction():
 def test_interaction_matrix_properties():
     """Rows of the pred_interactions layout sum to phi_i; the whole matrix sums
     to f(x); off-diagonal entries are SII/2 and symmetric."""
-    w = synth.single_config(3, n_samples=8, n_trees=10)
+    w = synth.workload("pairs-depth6", n_samples=8, n_trees=10)
     sii, phi = oracle.sii_exact(w.ens, w.X)
     mat = oracle.interaction_matrix(sii, phi)
     F = w.F
@@ -219,7 +219,7 @@ def test_alg1_threaded_equals_single_sample_dfs_and_exact():
     """The threaded Algorithm 1 runs the same DFS per row (bit-identical to
     the single-sample call, whatever the thread count) and, with 8 points on
     paths of at most 16 unique features, equals the exact expansion (Thm 2)."""
-    sub = synth.single_config(1, n_samples=9, n_trees=12)
+    sub = synth.workload("xgb-depth8", n_samples=9, n_trees=12)
     a = oracle.alg1_shap(sub.ens, sub.X, 8, n_threads=4)
     b = oracle.alg1_shap(sub.ens, sub.X, 8, n_threads=1)
     assert np.array_equal(a, b)
@@ -246,7 +246,7 @@ def test_quadrature_exact_iff_degree_covered():
 
 
 def test_eight_points_exact_on_depth8_config():
-    sub = synth.single_config(1, n_samples=10, n_trees=30)
+    sub = synth.workload("xgb-depth8", n_samples=10, n_trees=30)
     ref = oracle.shap_exact(sub.ens, sub.X)
     q = oracle.shap_quad(sub.ens, sub.X, 8)
     assert rel_err_rows(q, ref).max() < 1e-13
@@ -300,7 +300,7 @@ def test_gradient_leaf_subset_is_exact_at_listed_leaves():
 
 
 def test_threads_do_not_change_results():
-    w = synth.single_config(0)
+    w = synth.workload("small-depth4")
     a = oracle.shap_exact(w.ens, w.X, n_threads=1)
     b = oracle.shap_exact(w.ens, w.X, n_threads=7)
     assert np.array_equal(a, b)

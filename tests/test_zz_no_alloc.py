@@ -40,7 +40,7 @@ def _scale(ref):
 def test_noalloc_matches_workspace_entry_point_twice(qts):
     import torch
 
-    w = synth.single_config(3, n_samples=300, n_trees=60)
+    w = synth.workload("pairs-depth6", n_samples=300, n_trees=60)
     E = qts.Ensemble.from_arrays(w.ens)
     X = torch.from_numpy(w.X).cuda()
     M, F = w.X.shape
@@ -61,7 +61,7 @@ def test_noalloc_matches_workspace_entry_point_twice(qts):
 def test_noalloc_rejects_sizes_beyond_the_fixed_scratch(qts):
     import torch
 
-    w = synth.single_config(3, n_samples=8, n_trees=4)
+    w = synth.workload("pairs-depth6", n_samples=8, n_trees=4)
     E = qts.Ensemble.from_arrays(w.ens)
     F = w.X.shape[1]
     M = 5000  # (F(F-1)/2 + F) * M = 465 * 5000 > 2,097,152
