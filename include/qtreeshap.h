@@ -122,6 +122,31 @@ qts_status qts_shap_values(qts_ensemble *ens, const float *X, int64_t M, int32_t
                            int32_t n_quad, double *phi, qts_stream_t stream);
 
 /*
+ * qts_shap_values_alg1 - the same first-order Shapley values as qts_shap_values,
+ * computed by the depth-first traversal of Algorithm 1 (Sec. 5) instead of
+ * per-path products.  Each tree is walked once per sample: the products of the
+ * ancestors' merged factors a_f(t) = z_f + (o_f - z_f) t (Thm 1) at the
+ * quadrature nodes travel down, the subtrees' leaf sums travel up, and an edge
+ * on a feature already split on above it is telescoped against that ancestor
+ * (Eq. our_telescoping_background).  The work grows with the number of edges,
+ * not with the summed path lengths, which pays for deep trees whose paths share
+ * long prefixes.
+ *   Arguments, output layout and ownership as qts_shap_values (X device M x F
+ *   fp32 row-major; phi device M x (F+1) fp64, overwritten, phi[s][F] = E[f]).
+ *   Accumulation: FP32 over a chunk of trees per 32-sample tile, FP64 across
+ *   chunks.
+ * Errors: as qts_shap_values, plus QTS_ERR_UNSUPPORTED for an ensemble loaded
+ * with QTS_FLAG_FP64, for internal nodes more than 62 levels deep, or when the
+ * per-warp shared memory (about 2 KiB per tree level plus 260 bytes per
+ * feature) exceeds one block.  The first call on an ensemble (and the first
+ * after qts_update_params) builds the traversal program on the host and uploads
+ * it with cudaMalloc and a synchronous cudaMemcpy, so it must not be the first
+ * call inside a stream capture; later calls only enqueue on `stream`.
+ */
+qts_status qts_shap_values_alg1(qts_ensemble *ens, const float *X, int64_t M, int32_t F,
+                                int32_t n_quad, double *phi, qts_stream_t stream);
+
+/*
  * qts_shap_interactions - pairwise Shapley interaction values (Thm 1 with
  * S = {i,j}; Alg. 1 with s = 2) in the pred_interactions layout:
  *   phi_ij  device, M x (F+1) x (F+1) fp32, overwritten:

@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "QTS_OK", 1: "QTS_ERR_ARG", 2: "QTS_ERR_CUDA", 3: "QTS_ERR_OO
                 4: "QTS_ERR_UNSUPPORTED", 5: "QTS_ERR_TIMEOUT", 6: "QTS_ERR_DEVICE_CHECK"}
 
 # every symbol include/qtreeshap.h declares
-EXPORTS = ("qts_load_ensemble", "qts_update_params", "qts_shap_values", "qts_shap_interactions",
+EXPORTS = ("qts_load_ensemble", "qts_update_params", "qts_shap_values", "qts_shap_values_alg1",
+           "qts_shap_interactions",
            "qts_shap_interactions_noalloc", "qts_shap_interactions3",
            "qts_shap_backward", "qts_batched_fwd_bwd", "qts_autotune", "qts_sync_status",
            "qts_get_info", "qts_describe_ensemble", "qts_batched_kernel_count", "qts_batched_last_kernel_ms", "qts_gauss_legendre", "qts_last_error",
@@ -68,6 +69,7 @@ def lib():
                                         ctypes.POINTER(vp)]
         L.qts_update_params.argtypes = [vp, vp, vp]
         L.qts_shap_values.argtypes = [vp, vp, i64, i32, i32, vp, vp]
+        L.qts_shap_values_alg1.argtypes = [vp, vp, i64, i32, i32, vp, vp]
         L.qts_shap_interactions.argtypes = [vp, vp, i64, i32, i32, vp, vp]
         L.qts_shap_interactions_noalloc.argtypes = [vp, vp, i64, i32, i32, vp, vp]
         L.qts_shap_interactions3.argtypes = [vp, vp, i64, i32, i32, vp, vp]
@@ -212,6 +214,18 @@ def shap_values(ens: Ensemble, X, n_quad: int = 8, out=None, stream=None):
     if out is None:
         out = torch.empty((M, F + 1), dtype=torch.float64, device=X.device)
     _check(lib().qts_shap_values(ens.handle, _ptr(X), M, F, n_quad, _ptr(out), _stream(stream)))
+    return out
+
+
+def shap_values_alg1(ens: Ensemble, X, n_quad: int = 8, out=None, stream=None):
+    """Like shap_values, computed by the depth-first traversal of Algorithm 1."""
+    import torch
+
+    _check_x(ens, X)
+    M, F = X.shape
+    if out is None:
+        out = torch.empty((M, F + 1), dtype=torch.float64, device=X.device)
+    _check(lib().qts_shap_values_alg1(ens.handle, _ptr(X), M, F, n_quad, _ptr(out), _stream(stream)))
     return out
 
 

@@ -64,6 +64,7 @@ void release_device(qts_ensemble* e) {
     e->d_edge_coef = nullptr;
     e->d_empty_leaf = nullptr;
     e->device_bytes = 0;
+    release_dfs(e);
 }
 
 template <typename T>

@@ -118,6 +118,12 @@ struct qts_ensemble {
     // grow-only workspace (interaction accumulators, adjoint per-path sums)
     void* d_work = nullptr;
     size_t work_bytes = 0;
+    // depth-first (Algorithm 1) program: preorder records of the internal
+    // nodes, built on the first call that needs it
+    void* d_dfs = nullptr;
+    int64_t* d_dfs_off = nullptr;     // per tree, n_trees + 1
+    int dfs_levels = 0;               // internal-node depth + 1
+    int64_t dfs_records = 0;
     // per-width launch tuning (index = bucket width)
     qts::Tune tune[qts::kMaxD + 1];
     bool tuned = false;
@@ -131,6 +137,7 @@ qts_status cuda_fail(cudaError_t e, const char* what);
 qts_status ensure_workspace(qts_ensemble* e, size_t bytes);
 qts_status upload(qts_ensemble* e);
 void release_device(qts_ensemble* e);
+void release_dfs(qts_ensemble* e);      // drop the depth-first program (rebuilt on demand)
 int num_sms();
 void batch_forget(const qts_ensemble* e);  // drop cached batched graphs using e
 

@@ -15,8 +15,12 @@ Cases (synthetic inputs from `synth`):
                      model (1,000 trees, depth 16, F = 14, ~610 leaves per tree), 1,000 rows
   forward-deep20     qts_shap_values on 200 unbalanced trees of depth <= 20 over F = 24
                      (repeated features merged), M = 5,000
+  alg1-xgb, alg1-deep20, alg1-adultlike
+                     qts_shap_values_alg1 (depth-first form) on the same inputs as
+                     forward-xgb, forward-deep20 and forward-adultlike
 Prints the median CUDA-event time per call and the algorithmic FP32-pipe
-operation rate (4 ops per sample x element x node forward, 11 adjoint/fused).
+operation rate (4 ops per sample x element x node forward, 11 adjoint/fused;
+4 per sample x edge x node for the depth-first form).
 """
 from __future__ import annotations
 
@@ -40,7 +44,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["forward-xgb", "adjoint-xgb", "interactions-500", "fused-xgb",
                                      "fused-deep", "adjoint-deep", "interactions3-500",
-                                     "forward-adultlike", "forward-deep20"])
+                                     "forward-adultlike", "forward-deep20", "alg1-xgb", "alg1-deep20",
+                                     "alg1-adultlike"])
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     if args.case.endswith("-deep"):
@@ -52,12 +57,12 @@ def main():
         ens = synth.grow(es, 60, int(depth[e]), F, int(min(100000, 20 * 2 ** int(depth[e]))), 0.1, min_rows=5)
         w = synth.Workload("deep", ens, synth.normal(es, synth.STREAM_X, (4096, F)),
                            synth.normal(es, synth.STREAM_GRAD, (4096, F + 1)))
-    elif args.case == "forward-adultlike":
+    elif args.case in ("forward-adultlike", "alg1-adultlike"):
         seed = synth.SEED_BASE + 100
         ens = synth.grow(seed, 1000, 16, 14, 1850, 0.1, min_rows=5)
         w = synth.Workload("adultlike", ens, synth.normal(seed, synth.STREAM_X, (1000, 14)),
                            synth.normal(seed, synth.STREAM_GRAD, (1000, 15)))
-    elif args.case == "forward-deep20":
+    elif args.case in ("forward-deep20", "alg1-deep20"):
         w = synth.workload("deep-depth20", with_grad=True)
     else:
         w = synth.workload("pairs-depth6" if args.case.startswith("interactions") else "xgb-depth8",
@@ -80,6 +85,9 @@ def main():
         "interactions3-500": (lambda: qts.shap_interactions3(E, X, 8), 0),
         "forward-adultlike": (lambda: qts.shap_values(E, X, 8, out=phi), 4),
         "forward-deep20": (lambda: qts.shap_values(E, X, 8, out=phi), 4),
+        "alg1-xgb": (lambda: qts.shap_values_alg1(E, X, 8, out=phi), -4),
+        "alg1-deep20": (lambda: qts.shap_values_alg1(E, X, 8, out=phi), -4),
+        "alg1-adultlike": (lambda: qts.shap_values_alg1(E, X, 8, out=phi), -4),
     }[args.case]
     fn()
     torch.cuda.synchronize()
@@ -93,7 +101,10 @@ def main():
         ts.append(a.elapsed_time(b))
     E.sync_status()
     ms = float(np.median(ts))
-    work = ops * 8 * info["sum_unique"] * w.M
+    # path form: ops per (sample, merged element, node); depth-first form
+    # (negative): ops per (sample, edge, node), edges = nodes - trees
+    units = info["sum_unique"] if ops >= 0 else (E.n_nodes - w.ens.n_trees)
+    work = abs(ops) * 8 * units * w.M
     print(f"{args.case}: paths {info['n_paths']}, buckets {info['buckets']}")
     print(f"{args.case}: {ms:.3f} ms/call, {w.M * w.ens.n_trees / ms * 1e3:.3e} sample*trees/s"
           + (f", {work / ms / 1e9:.2f} Tops/s algorithmic" if ops else ""))
