@@ -64,6 +64,7 @@ typedef enum qts_status {
 #define QTS_MAX_FEATURES 640 /* sample and accumulator tiles live in shared memory */
 #define QTS_MAX_QUAD 32
 #define QTS_MAX_FEATURES_ORDER3 128
+#define QTS_MAX_CATEGORIES 64 /* categories 0..63 of a categorical split */
 
 /*
  * qts_load_ensemble - copy a tree ensemble and build its path tables.
@@ -98,6 +99,32 @@ qts_status qts_load_ensemble(int32_t n_trees, const int64_t *tree_node_offsets,
                              const float *threshold, const uint8_t *default_left, const float *z,
                              const float *leaf_value, int32_t n_features, uint32_t flags,
                              qts_ensemble **out);
+
+/*
+ * qts_load_ensemble_cat - qts_load_ensemble for ensembles with categorical
+ * splits (the paper's Adult models carry XGBoost categorical splits, Sec. 8).
+ * A categorical split on feature f sends x left iff x[f] is not NaN,
+ * 0 <= x[f] < QTS_MAX_CATEGORIES and bit floor(x[f]) of its mask is set; NaN
+ * follows default_left, every other value goes right.  Along a path the splits
+ * on one feature intersect (Eq. q_def: q_i depends on all splits on i), so a
+ * merged element holds the set of categories that satisfies all of them.
+ *   is_categorical       host, one per node: 1 if the node's split is
+ *                        categorical (ignored at leaves); NULL = none
+ *   category_left_mask   host, one per node: the categories that go left
+ *                        (ignored unless is_categorical); may be NULL only if
+ *                        is_categorical is NULL
+ *   other arguments      as qts_load_ensemble
+ * Errors: as qts_load_ensemble, plus QTS_ERR_ARG when a feature has both
+ * numerical and categorical splits in the ensemble.  Every entry point except
+ * qts_shap_values_alg1 (QTS_ERR_UNSUPPORTED) accepts such an ensemble;
+ * qts_update_params keeps the split types and masks.
+ */
+qts_status qts_load_ensemble_cat(int32_t n_trees, const int64_t *tree_node_offsets,
+                                 const int32_t *left, const int32_t *right, const int32_t *feature,
+                                 const float *threshold, const uint8_t *default_left, const float *z,
+                                 const float *leaf_value, const uint8_t *is_categorical,
+                                 const uint64_t *category_left_mask, int32_t n_features,
+                                 uint32_t flags, qts_ensemble **out);
 
 /*
  * qts_update_params - replace edge weights and leaf values (same topology) and

@@ -48,6 +48,8 @@ class _Ens(ctypes.Structure):
         ("default_left", ctypes.c_void_p),
         ("z", ctypes.c_void_p),
         ("leaf_value", ctypes.c_void_p),
+        ("is_cat", ctypes.c_void_p),
+        ("cat_left", ctypes.c_void_p),
     ]
 
 
@@ -97,7 +99,12 @@ class _Bound:
             np.ascontiguousarray(ens.leaf_value, dtype=np.float32),
         ]
         a = self.arrays
-        self.s = _Ens(len(a[0]) - 1, int(ens.n_features), *[x.ctypes.data for x in a])
+        is_cat = getattr(ens, "is_cat", None)
+        if is_cat is not None:
+            self.arrays += [np.ascontiguousarray(is_cat, dtype=np.uint8),
+                            np.ascontiguousarray(ens.cat_left, dtype=np.uint64)]
+        cat_ptrs = [x.ctypes.data for x in self.arrays[8:]] if is_cat is not None else [None, None]
+        self.s = _Ens(len(a[0]) - 1, int(ens.n_features), *[x.ctypes.data for x in a[:8]], *cat_ptrs)
         self.F = int(ens.n_features)
         self.N = int(a[0][-1])
 

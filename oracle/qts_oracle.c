@@ -67,11 +67,19 @@ int orc_gl_nodes(int n, double *t, double *w) {
 
 /* ============================================ tree basics (Sec. 2) ======= */
 
-/* Does x take the edge parent -> child?  x[f] < threshold goes left; a missing
- * (NaN) value goes the parent's default direction. */
+/* Category test of a categorical split: is v one of the categories in mask? */
+static int in_categories(uint64_t mask, float v) {
+    if (!(v >= 0.0f && v < 64.0f)) return 0;
+    return (int)((mask >> (int)v) & 1u);
+}
+
+/* Does x take the edge parent -> child?  x[f] < threshold goes left (a
+ * categorical split: x[f]'s category is in the left set); a missing (NaN)
+ * value goes the parent's default direction. */
 static int takes_left(const orc_ens *e, int64_t gnode, const float *x) {
     float v = x[e->feature[gnode]];
     if (isnan(v)) return e->default_left[gnode] != 0;
+    if (e->is_cat && e->is_cat[gnode]) return in_categories(e->cat_left[gnode], v);
     return v < e->threshold[gnode];
 }
 
@@ -103,6 +111,10 @@ typedef struct {
     int32_t feat;
     int32_t nan_ok;
     double z, lo, hi;
+    /* categorical splits merged in: x[f]'s category must be in `cats`; a value
+     * that is no category (outside [0, 64)) satisfies them only if other_ok */
+    int32_t has_cat, other_ok;
+    uint64_t cats;
     int64_t edge_begin, edge_end; /* into paths.edge_node */
 } pelem;
 
@@ -127,6 +139,8 @@ typedef struct {
     int32_t went_left;
     float thr;
     uint8_t def_left;
+    uint8_t is_cat;
+    uint64_t cat_left;
     double w;
     int64_t child; /* global node index */
 } split_rec;
@@ -172,11 +186,24 @@ static int paths_push(paths_t *P, int64_t *cap_p, int64_t *cap_e, int64_t *cap_g
         el->z = 1.0;
         el->lo = -INFINITY;
         el->hi = INFINITY;
+        el->has_cat = 0;
+        el->other_ok = 1;
+        el->cats = ~(uint64_t)0;
         el->edge_begin = P->n_edges;
         for (int k = 0; k < depth; ++k) {
             if (st[k].feat != feats[j]) continue;
             el->z *= st[k].w;
-            if (st[k].went_left) {
+            if (st[k].is_cat) {
+                /* left: the split's categories; right: all the others, and
+                 * every value that is no category */
+                el->has_cat = 1;
+                if (st[k].went_left) {
+                    el->cats &= st[k].cat_left;
+                    el->other_ok = 0;
+                } else {
+                    el->cats &= ~st[k].cat_left;
+                }
+            } else if (st[k].went_left) {
                 if ((double)st[k].thr < el->hi) el->hi = (double)st[k].thr;
             } else {
                 if ((double)st[k].thr > el->lo) el->lo = (double)st[k].thr;
@@ -218,6 +245,8 @@ static void walk(walk_ctx *W, int64_t base, int32_t v, int depth) {
         r->went_left = side == 0;
         r->thr = e->threshold[g];
         r->def_left = e->default_left[g];
+        r->is_cat = (e->is_cat && e->is_cat[g]) ? 1 : 0;
+        r->cat_left = r->is_cat ? e->cat_left[g] : 0;
         r->w = (double)e->z[base + c];
         r->child = base + c;
         walk(W, base, c, depth + 1);
@@ -251,7 +280,12 @@ static double satisfied(const pelem *el, const float *x) {
     float v = x[el->feat];
     if (isnan(v)) return el->nan_ok ? 1.0 : 0.0;
     double xv = (double)v;
-    return (el->lo <= xv && xv < el->hi) ? 1.0 : 0.0;
+    int ok = el->lo <= xv && xv < el->hi;
+    if (el->has_cat) {
+        int in_range = v >= 0.0f && v < 64.0f;
+        ok = ok && (in_range ? in_categories(el->cats, v) : el->other_ok);
+    }
+    return ok ? 1.0 : 0.0;
 }
 
 int orc_path_stats(const orc_ens *e, int64_t *n_paths, int32_t *max_d, int64_t *sum_d) {

@@ -46,6 +46,12 @@ typedef struct orc_ens {
     const uint8_t *default_left;
     const float *z;
     const float *leaf_value;
+    /* Categorical splits (both NULL when there are none): is_cat[n] = 1 makes
+     * node n's split categorical; cat_left[n] holds the categories 0..63 that
+     * go left.  x goes left iff it is not NaN, 0 <= x < 64 and bit floor(x) is
+     * set; NaN takes default_left; any other value goes right. */
+    const uint8_t *is_cat;
+    const uint64_t *cat_left;
 } orc_ens;
 
 int orc_gl_nodes(int n, double *t, double *w);

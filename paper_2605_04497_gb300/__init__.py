@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "QTS_OK", 1: "QTS_ERR_ARG", 2: "QTS_ERR_CUDA", 3: "QTS_ERR_OO
                 4: "QTS_ERR_UNSUPPORTED", 5: "QTS_ERR_TIMEOUT", 6: "QTS_ERR_DEVICE_CHECK"}
 
 # every symbol include/qtreeshap.h declares
-EXPORTS = ("qts_load_ensemble", "qts_update_params", "qts_shap_values", "qts_shap_values_alg1",
+EXPORTS = ("qts_load_ensemble", "qts_load_ensemble_cat", "qts_update_params", "qts_shap_values", "qts_shap_values_alg1",
            "qts_shap_interactions",
            "qts_shap_interactions_noalloc", "qts_shap_interactions3",
            "qts_shap_backward", "qts_batched_fwd_bwd", "qts_autotune", "qts_sync_status",
@@ -67,6 +67,8 @@ def lib():
         vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
         L.qts_load_ensemble.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, u32,
                                         ctypes.POINTER(vp)]
+        L.qts_load_ensemble_cat.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, u32,
+                                            ctypes.POINTER(ctypes.c_void_p)]
         L.qts_update_params.argtypes = [vp, vp, vp]
         L.qts_shap_values.argtypes = [vp, vp, i64, i32, i32, vp, vp]
         L.qts_shap_values_alg1.argtypes = [vp, vp, i64, i32, i32, vp, vp]
@@ -143,7 +145,7 @@ class Ensemble:
     """A tree ensemble loaded into device path tables (owns the C handle)."""
 
     def __init__(self, node_offsets, left, right, feature, threshold, default_left, z, leaf_value,
-                 n_features: int, fp64: bool = False):
+                 n_features: int, fp64: bool = False, is_cat=None, cat_left=None):
         arr = lambda a, dt: np.ascontiguousarray(a, dtype=dt)
         self._off = arr(node_offsets, np.int64)
         self._host = dict(left=arr(left, np.int32), right=arr(right, np.int32),
@@ -156,12 +158,17 @@ class Ensemble:
         self.fp64 = bool(fp64)
         h = ctypes.c_void_p()
         H = self._host
-        _check(lib().qts_load_ensemble(self.n_trees, self._off.ctypes.data, H["left"].ctypes.data,
-                                       H["right"].ctypes.data, H["feature"].ctypes.data,
-                                       H["threshold"].ctypes.data, H["default_left"].ctypes.data,
-                                       H["z"].ctypes.data, H["leaf_value"].ctypes.data,
-                                       self.n_features, QTS_FLAG_FP64 if fp64 else 0,
-                                       ctypes.byref(h)))
+        common = [self.n_trees, self._off.ctypes.data, H["left"].ctypes.data, H["right"].ctypes.data,
+                  H["feature"].ctypes.data, H["threshold"].ctypes.data, H["default_left"].ctypes.data,
+                  H["z"].ctypes.data, H["leaf_value"].ctypes.data]
+        flags = QTS_FLAG_FP64 if fp64 else 0
+        if is_cat is None:
+            _check(lib().qts_load_ensemble(*common, self.n_features, flags, ctypes.byref(h)))
+        else:
+            H["is_cat"] = arr(is_cat, np.uint8)
+            H["cat_left"] = arr(cat_left, np.uint64)
+            _check(lib().qts_load_ensemble_cat(*common, H["is_cat"].ctypes.data, H["cat_left"].ctypes.data,
+                                               self.n_features, flags, ctypes.byref(h)))
         self.handle = h
 
     @classmethod
@@ -169,7 +176,8 @@ class Ensemble:
         """From any object with node_offsets/left/right/feature/threshold/
         default_left/z/leaf_value/n_features attributes."""
         return cls(ens.node_offsets, ens.left, ens.right, ens.feature, ens.threshold,
-                   ens.default_left, ens.z, ens.leaf_value, ens.n_features, fp64=fp64)
+                   ens.default_left, ens.z, ens.leaf_value, ens.n_features, fp64=fp64,
+                   is_cat=getattr(ens, "is_cat", None), cat_left=getattr(ens, "cat_left", None))
 
     def update_params(self, z, leaf_value):
         z = np.ascontiguousarray(z, dtype=np.float32)

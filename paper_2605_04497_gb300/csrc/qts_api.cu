@@ -156,10 +156,11 @@ qts_status qts_gauss_legendre(int32_t n, double* t, double* w) {
     return gauss_legendre(n, t, w) ? QTS_OK : fail(QTS_ERR_ARG, "gauss_legendre failed");
 }
 
-qts_status qts_load_ensemble(int32_t n_trees, const int64_t* off, const int32_t* left,
-                             const int32_t* right, const int32_t* feature, const float* threshold,
-                             const uint8_t* default_left, const float* z, const float* leaf_value,
-                             int32_t n_features, uint32_t flags, qts_ensemble** out) {
+static qts_status load_impl(int32_t n_trees, const int64_t* off, const int32_t* left,
+                            const int32_t* right, const int32_t* feature, const float* threshold,
+                            const uint8_t* default_left, const float* z, const float* leaf_value,
+                            const uint8_t* is_cat, const uint64_t* cat_left, int32_t n_features,
+                            uint32_t flags, qts_ensemble** out) {
     if (!out) return fail(QTS_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (n_trees < 1 || !off || !left || !right || !feature || !threshold || !z || !leaf_value)
@@ -167,6 +168,7 @@ qts_status qts_load_ensemble(int32_t n_trees, const int64_t* off, const int32_t*
     if (n_features < 1 || n_features > QTS_MAX_FEATURES)
         return fail(QTS_ERR_UNSUPPORTED, "n_features must be in [1, " + std::to_string(QTS_MAX_FEATURES) + "]");
     if (flags & ~QTS_FLAG_FP64) return fail(QTS_ERR_ARG, "unknown flags");
+    if (is_cat && !cat_left) return fail(QTS_ERR_ARG, "category_left_mask is NULL");
     for (int t = 0; t < n_trees; ++t)
         if (off[t + 1] <= off[t]) return fail(QTS_ERR_ARG, "tree_node_offsets must be increasing");
     if (off[0] != 0) return fail(QTS_ERR_ARG, "tree_node_offsets[0] must be 0");
@@ -187,10 +189,16 @@ qts_status qts_load_ensemble(int32_t n_trees, const int64_t* off, const int32_t*
     e->leaf.assign(leaf_value, leaf_value + N);
     if (default_left) e->defl.assign(default_left, default_left + N);
     else e->defl.assign((size_t)N, 1);
+    if (is_cat) {
+        e->is_cat.assign(is_cat, is_cat + N);
+        e->cat_left.assign(cat_left, cat_left + N);
+    }
     std::string err;
     qts_status st = prepare(n_trees, e->off.data(), e->left.data(), e->right.data(),
                             e->feature.data(), e->thr.data(), e->defl.data(), e->z.data(),
-                            e->leaf.data(), n_features, (flags & QTS_FLAG_FP64) != 0, &e->prep, &err);
+                            e->leaf.data(), is_cat ? e->is_cat.data() : nullptr,
+                            is_cat ? e->cat_left.data() : nullptr, n_features,
+                            (flags & QTS_FLAG_FP64) != 0, &e->prep, &err);
     if (st != QTS_OK) {
         delete e;
         return fail(st, err);
@@ -212,6 +220,23 @@ qts_status qts_load_ensemble(int32_t n_trees, const int64_t* off, const int32_t*
     return QTS_OK;
 }
 
+qts_status qts_load_ensemble(int32_t n_trees, const int64_t* off, const int32_t* left,
+                             const int32_t* right, const int32_t* feature, const float* threshold,
+                             const uint8_t* default_left, const float* z, const float* leaf_value,
+                             int32_t n_features, uint32_t flags, qts_ensemble** out) {
+    return load_impl(n_trees, off, left, right, feature, threshold, default_left, z, leaf_value,
+                     nullptr, nullptr, n_features, flags, out);
+}
+
+qts_status qts_load_ensemble_cat(int32_t n_trees, const int64_t* off, const int32_t* left,
+                                 const int32_t* right, const int32_t* feature, const float* threshold,
+                                 const uint8_t* default_left, const float* z, const float* leaf_value,
+                                 const uint8_t* is_categorical, const uint64_t* category_left_mask,
+                                 int32_t n_features, uint32_t flags, qts_ensemble** out) {
+    return load_impl(n_trees, off, left, right, feature, threshold, default_left, z, leaf_value,
+                     is_categorical, category_left_mask, n_features, flags, out);
+}
+
 qts_status qts_update_params(qts_ensemble* e, const float* z, const float* leaf_value) {
     if (!e || !z || !leaf_value) return fail(QTS_ERR_ARG, "NULL argument");
     std::vector<float> z0 = e->z, l0 = e->leaf;
@@ -219,9 +244,12 @@ qts_status qts_update_params(qts_ensemble* e, const float* z, const float* leaf_
     e->leaf.assign(leaf_value, leaf_value + e->n_nodes);
     Prepared P;
     std::string err;
+    const bool cat = !e->is_cat.empty();
     qts_status st = prepare(e->n_trees, e->off.data(), e->left.data(), e->right.data(),
                             e->feature.data(), e->thr.data(), e->defl.data(), e->z.data(),
-                            e->leaf.data(), e->n_features, (e->flags & QTS_FLAG_FP64) != 0, &P, &err);
+                            e->leaf.data(), cat ? e->is_cat.data() : nullptr,
+                            cat ? e->cat_left.data() : nullptr, e->n_features,
+                            (e->flags & QTS_FLAG_FP64) != 0, &P, &err);
     if (st != QTS_OK) {
         e->z = z0;
         e->leaf = l0;
@@ -306,8 +334,8 @@ qts_status qts_describe_ensemble(int32_t n_trees, const int64_t* off, const int3
     std::string err;
     const bool fp64 = (flags & QTS_FLAG_FP64) != 0;
     qts_status st = prepare(n_trees, off, left, right, feature, threshold,
-                            default_left ? default_left : defl.data(), z, leaf_value, n_features,
-                            fp64, &P, &err);
+                            default_left ? default_left : defl.data(), z, leaf_value, nullptr, nullptr,
+                            n_features, fp64, &P, &err);
     if (st != QTS_OK) return fail(st, err);
     std::memset(out, 0, sizeof(*out));
     out->n_trees = n_trees;

@@ -508,7 +508,10 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
             ++kernels;
         }
         if (grad && err == cudaSuccess) err = cudaMemsetAsync(wbase, 0, bw.grad_bytes, cap);
-        if (err == cudaSuccess) err = cudaMemsetAsync(wbase + bw.flag_off, 0, 256, cap);
+        // the NaN flag starts set for ensembles with categorical elements, so
+        // their items take the NaN-aware (categorical-aware) variant
+        if (err == cudaSuccess)
+            err = cudaMemsetAsync(wbase + bw.flag_off, R.ens->prep.has_cat ? 1 : 0, 256, cap);
         if (R.M > 0 && err == cudaSuccess) {
             err = launch_transpose(R.X, R.M, R.F, R.F, (float*)(wbase + bw.xt_off), R.F + 1, bw.Mpad,
                                    (int*)(wbase + bw.flag_off), cap);

@@ -32,6 +32,7 @@ struct BwdArgs {
     const float* G;     // grad_phi, M x (F+1)
     int64_t M;
     int F;
+    int cat;            // ensemble has categorical elements: always the NaN-aware variant
     double* g_val;      // per path of this bucket
     double* g_slot;     // per element slot of this bucket (n_paths * D)
     double* phi;        // fused forward output (M x (F+1)) or nullptr
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(256) bwd_kernel(BwdArgs a) {
     }
     if (WITH_PHI)
         for (int idx = threadIdx.x; idx < (F + 1) * kTileLd; idx += blockDim.x) ps[idx] = 0.f;
-    const bool has_nan = load_tile_t(xs, a.X, s0, a.M, F, F, 1);
+    const bool has_nan = load_tile_t(xs, a.X, s0, a.M, F, F, 1) || a.cat != 0;
     // grad_phi tile: columns 0..F-1 (column F, the bias weight, is handled in
     // the epilogue); row F stays zero for padding elements
     load_tile_t(gs, a.G, s0, a.M, F, F + 1, 1);
@@ -241,6 +242,7 @@ cudaError_t launch_bwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
     a.G = grad;
     a.M = M;
     a.F = F;
+    a.cat = e->prep.has_cat ? 1 : 0;
     a.g_val = g_val + b.path_base;
     a.g_slot = g_slot + b.slot_base;
     a.phi = phi;

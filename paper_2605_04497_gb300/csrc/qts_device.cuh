@@ -89,6 +89,20 @@ __device__ __forceinline__ int feat_of(uint32_t bits) { return (int)(bits & kFea
 // all send missing values the way the path goes.
 template <bool HAS_NAN>
 __device__ __forceinline__ bool satisfies(float x, float lo, float hi, uint32_t bits) {
+    if constexpr (HAS_NAN) {
+        // categorical element (only in ensembles that have them, which always
+        // take this variant): x's category in the merged set; NaN by the
+        // merged default direction; other values by kOtherOk
+        if (bits & kCat) {
+            if (x != x) return (bits & kNanOk) != 0;
+            if (x >= 0.f && x < 64.f) {
+                const int c = (int)x;
+                const uint32_t w = __float_as_uint(c < 32 ? lo : hi);
+                return ((w >> (c & 31)) & 1u) != 0;
+            }
+            return (bits & kOtherOk) != 0;
+        }
+    }
     bool o = (x >= lo) && (x < hi);
     if (HAS_NAN) o = o || ((x != x) && (bits & kNanOk));
     return o;

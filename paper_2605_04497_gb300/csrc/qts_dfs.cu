@@ -478,6 +478,8 @@ extern "C" qts_status qts_shap_values_alg1(qts_ensemble* e, const float* X, int6
     if (st != QTS_OK) return st;
     if (e->flags & QTS_FLAG_FP64)
         return fail(QTS_ERR_UNSUPPORTED, "the depth-first form runs on FP32 ensembles only");
+    if (!e->is_cat.empty())
+        return fail(QTS_ERR_UNSUPPORTED, "the depth-first form has no categorical splits");
     if (M == 0) return QTS_OK;
     if (!phi) return fail(QTS_ERR_ARG, "phi is NULL");
     st = build_dfs_program(e);

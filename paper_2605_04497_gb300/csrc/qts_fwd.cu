@@ -26,6 +26,7 @@ struct FwdArgs {
     const float* X;
     int64_t M;
     int F;
+    int cat;            // ensemble has categorical elements: always the NaN-aware variant
     double* phi;        // M x (F+1)
     int* status;
     int ntiles;         // sample tiles of 32 per block: 1 (warps share the tile and
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
     }
     for (int idx = threadIdx.x; idx < a.ntiles * stride; idx += blockDim.x) ps[idx] = (Acc)0;
     // sample tiles (row = feature, column = sample) plus a zero row F for padding
-    const bool has_nan = load_tiles_t(xs, a.X, s0, a.M, F, F, 1, a.ntiles, stride);
+    const bool has_nan = load_tiles_t(xs, a.X, s0, a.M, F, F, 1, a.ntiles, stride) || a.cat != 0;
 
     const bool ok = stream_paths<Rec, D>(
         (const Rec*)a.rec, p0, p1, a.sub, st0, st1, bars, s_phase, &s_flag, a.status,
@@ -206,6 +207,7 @@ cudaError_t launch_fwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
     a.X = X;
     a.M = M;
     a.F = F;
+    a.cat = e->prep.has_cat ? 1 : 0;
     a.phi = phi;
     a.status = e->d_status;
     a.q = q;

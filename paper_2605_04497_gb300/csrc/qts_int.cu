@@ -34,6 +34,7 @@ struct IntArgs {
     const float* X;
     int64_t M;
     int F;
+    int cat;            // ensemble has categorical elements: always the NaN-aware variant
     int64_t n_pairs;
     double* acc_pair;   // [n_pairs][M]
     double* acc_phi;    // [F][M]
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(256) int_kernel(IntArgs a) {
     for (int idx = threadIdx.x; idx < (int)rows * kTileLd; idx += blockDim.x) ps[idx] = 0.f;
     if (PAIR_SMEM)
         for (int64_t idx = threadIdx.x; idx < a.n_pairs * kTileLd; idx += blockDim.x) pt[idx] = 0.f;
-    const bool has_nan = load_tile_t(xs, a.X, s0, a.M, F, F, 1);
+    const bool has_nan = load_tile_t(xs, a.X, s0, a.M, F, F, 1) || a.cat != 0;
     const int64_t s = s0 + lane;
 
     const bool ok = stream_paths<Rec32, D>(
@@ -257,6 +258,7 @@ cudaError_t launch_int_bucket(const qts_ensemble* e, const Bucket& b, const floa
     a.X = X;
     a.M = M;
     a.F = F;
+    a.cat = e->prep.has_cat ? 1 : 0;
     a.n_pairs = (int64_t)F * (F - 1) / 2;
     a.acc_pair = acc_pair;
     a.acc_phi = acc_phi;

@@ -33,6 +33,7 @@ struct Int3Args {
     const float* X;
     int64_t M;
     int F;
+    int cat;            // ensemble has categorical elements: always the NaN-aware variant
     double* acc;        // [n_triples][M]
     int* status;
     QuadF q;
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(256) int3_kernel(Int3Args a) {
         mbar_fence_init();
         s_phase[0] = s_phase[1] = 0;
     }
-    const bool has_nan = load_tile_t(xs, a.X, s0, a.M, F, F, 1);
+    const bool has_nan = load_tile_t(xs, a.X, s0, a.M, F, F, 1) || a.cat != 0;
     const int64_t s = s0 + lane;
     (void)stream_paths<Rec32, D>(a.rec, p0, p1, a.sub, st0, st1, bars, s_phase, &s_flag, a.status,
                                  [&](int64_t, const Rec32* r) {
@@ -191,6 +192,7 @@ static cudaError_t launch_int3_bucket(const qts_ensemble* e, const Bucket& b, co
     a.X = X;
     a.M = M;
     a.F = F;
+    a.cat = e->prep.has_cat ? 1 : 0;
     a.acc = acc;
     a.status = e->d_status;
     a.q = q;

@@ -25,6 +25,11 @@ struct __align__(16) Rec32 {
     uint32_t bits;
 };
 constexpr uint32_t kNanOk = 0x80000000u;
+// Categorical element: lo and hi hold the low and high 32 bits of the set of
+// categories that satisfy every split merged into it, kOtherOk says whether a
+// value that is not a category (outside [0, 64)) satisfies them.
+constexpr uint32_t kCat = 0x40000000u;
+constexpr uint32_t kOtherOk = 0x20000000u;
 constexpr uint32_t kFeatMask = 0x00FFFFFFu;
 
 // FP64 table: 32-byte records {z, 0, lo, hi, bits, 0}; header {val, prod z}.
@@ -67,13 +72,15 @@ struct Prepared {
     int64_t n_paths = 0, n_slots = 0, n_leaves = 0, sum_unique = 0;
     int max_unique = 0;
     double bias = 0.0;  // E[f]
+    bool has_cat = false;  // some element is categorical: kernels take their NaN-aware variant
 };
 
 // Prepare the path tables (host, multi-threaded).  Returns QTS_OK or an error
 // with the message in *err.
 qts_status prepare(int32_t n_trees, const int64_t* off, const int32_t* left, const int32_t* right,
                    const int32_t* feature, const float* thr, const uint8_t* defl, const float* z,
-                   const float* leaf, int32_t F, bool fp64, Prepared* out, std::string* err);
+                   const float* leaf, const uint8_t* is_cat, const uint64_t* cat_left, int32_t F,
+                   bool fp64, Prepared* out, std::string* err);
 
 // Gauss-Legendre nodes on [0,1] (Golub-Welsch via Jacobi eigen-decomposition).
 bool gauss_legendre(int n, double* t, double* w);
@@ -101,6 +108,8 @@ struct qts_ensemble {
     std::vector<int32_t> left, right, feature;
     std::vector<float> thr, z, leaf;
     std::vector<uint8_t> defl;
+    std::vector<uint8_t> is_cat;      // empty: no categorical splits
+    std::vector<uint64_t> cat_left;
     // prepared tables
     qts::Prepared prep;
     // device memory

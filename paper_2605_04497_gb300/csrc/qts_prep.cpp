@@ -106,8 +106,9 @@ namespace {
 
 struct EdgeRec {
     int32_t feat;
-    uint8_t went_left, def_left;
+    uint8_t went_left, def_left, is_cat;
     float thr;
+    uint64_t cats;  // categorical edge: the categories that take it
     double w;
     int64_t child;  // global node index
 };
@@ -115,8 +116,10 @@ struct EdgeRec {
 struct ElemTmp {
     int32_t feat;
     uint8_t nan_ok;
+    uint8_t is_cat, other_ok;  // categorical: the set is `cats`, plus "other" values if other_ok
     double z;
     float lo, hi;
+    uint64_t cats;
     int32_t edge_off, edge_cnt;  // into the thread's edge list
 };
 
@@ -142,7 +145,7 @@ struct ThreadOut {
 
 void extract_trees(int t0, int t1, const int64_t* off, const int32_t* left, const int32_t* right,
                    const int32_t* feature, const float* thr, const uint8_t* defl, const float* z,
-                   const float* leaf, ThreadOut* out) {
+                   const float* leaf, const uint8_t* is_cat, const uint64_t* cat_left, ThreadOut* out) {
     std::vector<EdgeRec> path;
     struct Item { int32_t v; int32_t depth; EdgeRec in; };
     std::vector<Item> stack;
@@ -191,14 +194,23 @@ void extract_trees(int t0, int t1, const int64_t* off, const int32_t* left, cons
                             return;
                         }
                         slot = d++;
-                        merged[slot] = {e.feat, 1, 1.0, -INFINITY, INFINITY, 0, 0};
+                        merged[slot] = {e.feat, 1, 0, 1, 1.0, -INFINITY, INFINITY, ~0ull, 0, 0};
                         medges[slot].clear();
                         mw[slot].clear();
                     }
                     ElemTmp& m = merged[slot];
                     m.z *= e.w;
-                    if (e.went_left) m.hi = std::min(m.hi, e.thr);
-                    else m.lo = std::max(m.lo, e.thr);
+                    if (e.is_cat) {
+                        // the categories that satisfy every split so far; values
+                        // that are not categories only ever take right edges
+                        m.is_cat = 1;
+                        m.cats &= e.cats;
+                        if (e.went_left) m.other_ok = 0;
+                    } else if (e.went_left) {
+                        m.hi = std::min(m.hi, e.thr);
+                    } else {
+                        m.lo = std::max(m.lo, e.thr);
+                    }
                     if (e.went_left != e.def_left) m.nan_ok = 0;
                     medges[slot].push_back(e.child);
                     mw[slot].push_back(e.w);
@@ -238,6 +250,8 @@ void extract_trees(int t0, int t1, const int64_t* off, const int32_t* left, cons
                 e.feat = f;
                 e.went_left = side == 0;
                 e.def_left = defl ? (defl[g] != 0) : 1;
+                e.is_cat = (is_cat && is_cat[g]) ? 1 : 0;
+                e.cats = e.is_cat ? (side == 0 ? cat_left[g] : ~cat_left[g]) : ~0ull;
                 e.thr = thr[g];
                 e.w = (double)z[base + c];
                 e.child = base + c;
@@ -247,11 +261,40 @@ void extract_trees(int t0, int t1, const int64_t* off, const int32_t* left, cons
     }
 }
 
+// Record fields of a merged element: numerical [lo, hi), or for a categorical
+// one the category set's low and high 32 bits in lo and hi (bit patterns).
+uint32_t elem_bits(const ElemTmp& m, float* lo, float* hi) {
+    uint32_t bits = (uint32_t)m.feat | (m.nan_ok ? kNanOk : 0u);
+    if (m.is_cat) {
+        const uint32_t l = (uint32_t)(m.cats & 0xFFFFFFFFull), h = (uint32_t)(m.cats >> 32);
+        std::memcpy(lo, &l, 4);
+        std::memcpy(hi, &h, 4);
+        return bits | kCat | (m.other_ok ? kOtherOk : 0u);
+    }
+    *lo = m.lo;
+    *hi = m.hi;
+    return bits;
+}
+
 }  // namespace
 
 static qts_status validate(int32_t n_trees, const int64_t* off, const int32_t* left,
                            const int32_t* right, const int32_t* feature, const float* thr,
-                           const float* z, const float* leaf, int32_t F, std::string* err) {
+                           const float* z, const float* leaf, const uint8_t* is_cat,
+                           const uint64_t* cat_left, int32_t F, std::string* err) {
+    if (is_cat && !cat_left) { *err = "category_left_mask is NULL"; return QTS_ERR_ARG; }
+    if (is_cat) {
+        // a feature is either numerical or categorical throughout the ensemble
+        std::vector<uint8_t> kind((size_t)F, 0);  // bit 0 numerical, bit 1 categorical
+        for (int64_t g = 0; g < off[n_trees]; ++g) {
+            if (left[g] < 0 || feature[g] < 0 || feature[g] >= F) continue;
+            kind[feature[g]] |= is_cat[g] ? 2 : 1;
+            if (kind[feature[g]] == 3) {
+                *err = "feature " + std::to_string(feature[g]) + " has numerical and categorical splits";
+                return QTS_ERR_ARG;
+            }
+        }
+    }
     if (off[0] != 0) { *err = "tree_node_offsets[0] must be 0"; return QTS_ERR_ARG; }
     for (int t = 0; t < n_trees; ++t) {
         int64_t a = off[t], b = off[t + 1];
@@ -288,8 +331,9 @@ static qts_status validate(int32_t n_trees, const int64_t* off, const int32_t* l
 
 qts_status prepare(int32_t n_trees, const int64_t* off, const int32_t* left, const int32_t* right,
                    const int32_t* feature, const float* thr, const uint8_t* defl, const float* z,
-                   const float* leaf, int32_t F, bool fp64, Prepared* P, std::string* err) {
-    qts_status st = validate(n_trees, off, left, right, feature, thr, z, leaf, F, err);
+                   const float* leaf, const uint8_t* is_cat, const uint64_t* cat_left, int32_t F,
+                   bool fp64, Prepared* P, std::string* err) {
+    qts_status st = validate(n_trees, off, left, right, feature, thr, z, leaf, is_cat, cat_left, F, err);
     if (st != QTS_OK) return st;
     *P = Prepared();
     int64_t total_nodes = off[n_trees];
@@ -310,7 +354,7 @@ qts_status prepare(int32_t n_trees, const int64_t* off, const int32_t* left, con
         std::vector<std::thread> th;
         for (int k = 0; k < nth; ++k)
             th.emplace_back(extract_trees, cut[k], cut[k + 1], off, left, right, feature, thr, defl,
-                            z, leaf, &outs[k]);
+                            z, leaf, is_cat, cat_left, &outs[k]);
         for (auto& x : th) x.join();
     }
     for (auto& o : outs)
@@ -378,8 +422,10 @@ qts_status prepare(int32_t n_trees, const int64_t* off, const int32_t* left, con
                 for (int j = 0; j < D; ++j) {
                     if (j < p.d) {
                         const ElemTmp& m = o.elems[p.el_off + j];
-                        P->rec64[r + 1 + j] = {m.z, 0.0, m.lo, m.hi,
-                                               (uint32_t)m.feat | (m.nan_ok ? kNanOk : 0u), 0u};
+                        float lo, hi;
+                        const uint32_t bits = elem_bits(m, &lo, &hi);
+                        if (m.is_cat) P->has_cat = true;
+                        P->rec64[r + 1 + j] = {m.z, 0.0, lo, hi, bits, 0u};
                     } else {
                         P->rec64[r + 1 + j] = {1.0, 0.0, -INFINITY, INFINITY, pad_bits, 0u};
                     }
@@ -389,8 +435,10 @@ qts_status prepare(int32_t n_trees, const int64_t* off, const int32_t* left, con
                 for (int j = 0; j < D; ++j) {
                     if (j < p.d) {
                         const ElemTmp& m = o.elems[p.el_off + j];
-                        P->rec32[r + 1 + j] = {(float)m.z, m.lo, m.hi,
-                                               (uint32_t)m.feat | (m.nan_ok ? kNanOk : 0u)};
+                        float lo, hi;
+                        const uint32_t bits = elem_bits(m, &lo, &hi);
+                        if (m.is_cat) P->has_cat = true;
+                        P->rec32[r + 1 + j] = {(float)m.z, lo, hi, bits};
                     } else {
                         P->rec32[r + 1 + j] = {1.f, -INFINITY, INFINITY, pad_bits};
                     }

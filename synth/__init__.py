@@ -94,7 +94,7 @@ class Ensemble:
     each tree; tree t owns nodes [node_offsets[t], node_offsets[t+1])."""
 
     def __init__(self, node_offsets, left, right, feature, threshold, default_left, z,
-                 leaf_value, cover, n_features, max_depth_seen=None):
+                 leaf_value, cover, n_features, max_depth_seen=None, is_cat=None, cat_left=None):
         self.node_offsets = np.ascontiguousarray(node_offsets, dtype=np.int64)
         self.left = np.ascontiguousarray(left, dtype=np.int32)
         self.right = np.ascontiguousarray(right, dtype=np.int32)
@@ -106,6 +106,10 @@ class Ensemble:
         self.cover = np.ascontiguousarray(cover, dtype=np.int32)
         self.n_features = int(n_features)
         self.max_depth_seen = max_depth_seen
+        # categorical splits (None: all splits numerical): is_cat[n] = 1 makes
+        # node n's split categorical, cat_left[n] the categories 0..63 going left
+        self.is_cat = None if is_cat is None else np.ascontiguousarray(is_cat, dtype=np.uint8)
+        self.cat_left = None if cat_left is None else np.ascontiguousarray(cat_left, dtype=np.uint64)
 
     @property
     def n_trees(self) -> int:
@@ -121,9 +125,12 @@ class Ensemble:
 
     def tree(self, t: int) -> "Ensemble":
         a, b = self.node_offsets[t], self.node_offsets[t + 1]
+        cat = self.is_cat is not None
         return Ensemble([0, b - a], self.left[a:b], self.right[a:b], self.feature[a:b],
                         self.threshold[a:b], self.default_left[a:b], self.z[a:b],
-                        self.leaf_value[a:b], self.cover[a:b], self.n_features)
+                        self.leaf_value[a:b], self.cover[a:b], self.n_features,
+                        is_cat=self.is_cat[a:b] if cat else None,
+                        cat_left=self.cat_left[a:b] if cat else None)
 
     def subset(self, trees) -> "Ensemble":
         parts = [self.tree(int(t)) for t in trees]
@@ -133,7 +140,9 @@ class Ensemble:
         return Ensemble(self.node_offsets.copy(), self.left.copy(), self.right.copy(),
                         self.feature.copy(), self.threshold.copy(), self.default_left.copy(),
                         self.z.copy(), self.leaf_value.copy(), self.cover.copy(), self.n_features,
-                        self.max_depth_seen)
+                        self.max_depth_seen,
+                        is_cat=None if self.is_cat is None else self.is_cat.copy(),
+                        cat_left=None if self.cat_left is None else self.cat_left.copy())
 
 
 def concat(parts) -> Ensemble:
@@ -141,9 +150,54 @@ def concat(parts) -> Ensemble:
     for p in parts:
         offs.append(offs[-1] + p.n_nodes)
     cat = lambda name: np.concatenate([getattr(p, name) for p in parts])
+    kw = {}
+    if any(p.is_cat is not None for p in parts):
+        kw["is_cat"] = np.concatenate([p.is_cat if p.is_cat is not None else np.zeros(p.n_nodes, np.uint8)
+                                       for p in parts])
+        kw["cat_left"] = np.concatenate([p.cat_left if p.cat_left is not None
+                                         else np.zeros(p.n_nodes, np.uint64) for p in parts])
     return Ensemble(np.array(offs, dtype=np.int64), cat("left"), cat("right"), cat("feature"),
                     cat("threshold"), cat("default_left"), cat("z"), cat("leaf_value"),
-                    cat("cover"), max(p.n_features for p in parts))
+                    cat("cover"), max(p.n_features for p in parts), **kw)
+
+
+def make_categorical(ens: Ensemble, features, n_categories: int, seed: int) -> Ensemble:
+    """A copy of `ens` whose splits on `features` are categorical: each such
+    node sends a random non-empty proper subset of the categories 0..n-1 left
+    (numpy PCG64 stream `seed`).  Edge weights are kept as they are (any
+    positive weights are valid inputs)."""
+    out = ens.copy()
+    rng = np.random.default_rng(seed)
+    is_cat = np.zeros(out.n_nodes, np.uint8)
+    cat_left = np.zeros(out.n_nodes, np.uint64)
+    full = (1 << n_categories) - 1
+    for g in range(out.n_nodes):
+        if out.left[g] >= 0 and int(out.feature[g]) in set(features):
+            m = 0
+            while m == 0 or m == full:
+                m = int(sum(1 << c for c in range(n_categories) if rng.random() < 0.5))
+            is_cat[g] = 1
+            cat_left[g] = m
+    out.is_cat, out.cat_left = is_cat, cat_left
+    return out
+
+
+def categorical_columns(X: np.ndarray, features, n_categories: int, seed: int,
+                        other_frac: float = 0.1, nan_frac: float = 0.1) -> np.ndarray:
+    """A copy of X whose `features` columns hold categories 0..n-1, with a
+    fraction of values that are no category (negative, >= n, or >= 64) and a
+    fraction of NaN."""
+    out = np.array(X, dtype=np.float32, copy=True)
+    rng = np.random.default_rng(seed)
+    for f in features:
+        col = rng.integers(0, n_categories, X.shape[0]).astype(np.float32)
+        u = rng.random(X.shape[0])
+        other = rng.choice(np.array([-1.0, -0.5, n_categories, n_categories + 0.5, 64.0, 1e6],
+                                    dtype=np.float32), X.shape[0])
+        col = np.where(u < other_frac, other, col)
+        col = np.where((u >= other_frac) & (u < other_frac + nan_frac), np.nan, col)
+        out[:, f] = col
+    return out
 
 
 def grow(seed: int, n_trees: int, max_depth: int, n_features: int, n_train: int,

@@ -56,3 +56,24 @@ def leaf_unique_counts(ens):
             stack.append((int(ens.left[g]), nxt))
             stack.append((int(ens.right[g]), nxt))
     return out
+
+
+def golden_categorical_trees():
+    with open(os.path.join(GOLDEN, "categorical_trees.json")) as fh:
+        data = json.load(fh)
+    out = []
+    for t in data["trees"]:
+        n = len(t["left"])
+        ens = synth.Ensemble([0, n], t["left"], t["right"], t["feature"], t["threshold"],
+                             t["default_left"], t["z"], t["leaf_value"], np.zeros(n), t["n_features"],
+                             is_cat=t["is_cat"], cat_left=t["cat_left"])
+        out.append((t, ens))
+    return out
+
+
+def categorical_ensemble(seed, n_trees=3, depth=7, F=5, cat_features=(0, 2), n_categories=6,
+                         n_train=500):
+    """Seeded ensemble whose splits on `cat_features` are categorical (random
+    left sets over n_categories), depth > F so features repeat on paths."""
+    base = synth.grow(seed, n_trees, depth, F, n_train, 1.0, min_rows=2)
+    return synth.make_categorical(base, cat_features, n_categories, seed + 1)

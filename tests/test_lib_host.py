@@ -118,3 +118,17 @@ def test_triple_index_is_the_lexicographic_rank():
         idx = qts.triple_index(F)
         lex = [(a, b, c) for a in range(F) for b in range(a + 1, F) for c in range(b + 1, F)]
         assert [idx[t] for t in lex] == list(range(len(lex)))
+
+
+def test_feature_with_both_split_types_is_rejected():
+    """A feature is either numerical or categorical throughout an ensemble; the
+    loader rejects a mix before touching the device."""
+    from helpers import categorical_ensemble
+
+    ens = categorical_ensemble(2300, n_trees=2, depth=5, F=3, cat_features=(0,))
+    internal = np.flatnonzero((ens.left >= 0) & (ens.feature == 0))
+    assert len(internal) >= 2
+    ens.is_cat[internal[0]] = 0  # one numerical split on a categorical feature
+    with pytest.raises(qts.QtsError) as ei:
+        qts.Ensemble.from_arrays(ens)
+    assert ei.value.status == 1 and "numerical and categorical" in str(ei.value)

@@ -332,3 +332,42 @@ def test_third_order_alg1_exact_at_theorem2_bound():
     for s in range(2):
         got = oracle.alg1(ens, X[s], 3, n)
         assert np.abs(got - ref[s]).max() < 1e-12 * max(1.0, np.abs(ref[s]).max())
+
+
+# ------------------------------------------------------------ categorical splits
+
+def test_golden_categorical_trees():
+    """Hand-derived values with categorical splits: a stump (category in the
+    set, a fractional value, values that are no category, NaN) and a feature
+    whose two categorical splits intersect along a path."""
+    from helpers import golden_categorical_trees
+
+    for spec, ens in golden_categorical_trees():
+        for s in spec["samples"]:
+            x = sample_x(s)
+            want = np.array(s["phi"])
+            bf_phi, _ = oracle.brute_force(ens, x)
+            ex = oracle.shap_exact(ens, x[None])[0]
+            a1 = oracle.alg1(ens, x, 1, 8)
+            for got in (bf_phi, ex, a1):
+                assert np.allclose(got, want, atol=1e-15, rtol=0), (spec["name"], s["x"], got, want)
+            assert oracle.predict(ens, x[None])[0] == s["fx"]
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_categorical_exact_equals_brute_force(seed):
+    """The merged category sets of the exact expansion against subset
+    enumeration of the game, which follows each categorical split on its own;
+    inputs include values that are no category and NaN."""
+    from helpers import categorical_ensemble
+
+    ens = categorical_ensemble(1700 + seed, n_trees=2, depth=7, F=5)
+    X = synth.categorical_columns(synth.normal(1700 + seed, 1, (6, 5)), (0, 2), 6, 1700 + seed)
+    ex_sii, ex_phi = oracle.sii_exact(ens, X)
+    for s in range(X.shape[0]):
+        bf_phi, bf_sii = oracle.brute_force(ens, X[s])
+        assert np.allclose(ex_phi[s], bf_phi, atol=1e-13, rtol=0)
+        assert np.allclose(ex_sii[s], bf_sii, atol=1e-13, rtol=0)
+    assert np.allclose(ex_phi.sum(axis=1), oracle.predict(ens, X), atol=1e-12)
+    a1 = np.stack([oracle.alg1(ens, X[s], 1, 8) for s in range(X.shape[0])])
+    assert np.allclose(a1, ex_phi, atol=1e-12)
