@@ -202,40 +202,63 @@ __device__ __forceinline__ void dfs_fetch(const float4* stk, int level, int part
     v[3] = make_float2(b.z, b.w);
 }
 
-// One tree for the warp's 32 samples and one node group.
-__device__ void dfs_tree(const DfsRec* __restrict__ rec, int64_t nrec, const float* xs, float* tile,
+template <typename MaskT>
+__device__ __forceinline__ bool dfs_bit(MaskT m, int k) {
+    return ((m >> k) & (MaskT)1) != 0;
+}
+
+template <typename MaskT>
+__device__ __forceinline__ MaskT dfs_setbit(MaskT m, int k, bool v) {
+    return (m & ~((MaskT)1 << k)) | ((MaskT)v << k);
+}
+
+__device__ __forceinline__ float dfs_sum(const float2 (&C)[4]) {
+    const float2 s = add2(add2(C[0], C[1]), add2(C[2], C[3]));
+    return s.x + s.y;
+}
+
+// One tree for the warp's 32 samples and one node group.  MaskT holds one bit
+// per level (uint32_t when the trees are at most 32 internal levels deep).
+template <typename MaskT>
+__device__ void dfs_tree(const DfsRec* __restrict__ rec, int nrec, const float* xs, float* tile,
                          float4* stk, int* lvl, int lane, const float2 (&T)[4], const float2 (&W)[4]) {
-    float2 C[4], G[4];
+    float2 C[4], G[4], R[4], Rp[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         C[p] = W[p];
         G[p] = f2s(0.f);
+        R[p] = Rp[p] = f2s(1.f);  // only read at repeated features, where they are set
     }
-    uint64_t om = 0, gm = 0;  // per level: merged o of the edge taken, and "x goes left"
-    const float2 none[4] = {f2s(1.f), f2s(1.f), f2s(1.f), f2s(1.f)};
-    for (int64_t i = 0; i < nrec; ++i) {
-        const DfsRec r = dfs_load(rec + i);
+    MaskT om = 0, gm = 0;  // per level: merged o of the edge taken, and "x goes left"
+    DfsRec rn = dfs_load(rec);
+    for (int i = 0; i < nrec; ++i) {
+        const DfsRec r = rn;
+        if (i + 1 < nrec) rn = dfs_load(rec + i + 1);  // next record, in flight during this one
         const DfsMeta m = dfs_meta(r);
         const float x = xs[m.f * 33 + lane];
         const bool gl = (x != x) ? m.dl : (x < r.thr);
         const bool rep = m.anc != (int)kDfsNoAnc;
-        const bool oold = rep ? ((om >> m.anc) & 1ull) != 0 : true;
-        const float d0 = ((gl && oold) ? 1.f : 0.f) - r.zc[0];
-        const float d1 = ((!gl && oold) ? 1.f : 0.f) - r.zc[1];
-        float2 R[4] = {none[0], none[1], none[2], none[3]};
+        const float ol = (!rep || dfs_bit(om, m.anc)) ? 1.f : 0.f;  // merged o above the node
+        const float o0 = gl ? ol : 0.f;
+        const float d0 = o0 - r.zc[0], d1 = (ol - o0) - r.zc[1];
         float dold = 0.f;
         if (rep) {
-            dold = (oold ? 1.f : 0.f) - r.zold;
+            dold = ol - r.zold;
             dfs_rold(T, r.zold, dold, R);
         }
         if (m.leaf0 || m.leaf1) {
-            float c = 0.f;
-            if (rep) {
+            float c;
+            if (!rep) {
+                // both leaf children at once: G += val (z + d t), phi_f += val d sum(C)
+                const float vd = (m.leaf0 ? r.val[0] * d0 : 0.f) + (m.leaf1 ? r.val[1] * d1 : 0.f);
+                const float vz = (m.leaf0 ? r.val[0] * r.zc[0] : 0.f) + (m.leaf1 ? r.val[1] * r.zc[1] : 0.f);
+                c = vd * dfs_sum(C);
+#pragma unroll
+                for (int p = 0; p < 4; ++p) G[p] = fma2(T[p], f2s(vd), add2(G[p], f2s(vz)));
+            } else {
+                c = 0.f;
                 if (m.leaf0) c += dfs_leaf<true>(T, C, r.zc[0], d0, r.val[0], R, dold, G);
                 if (m.leaf1) c += dfs_leaf<true>(T, C, r.zc[1], d1, r.val[1], R, dold, G);
-            } else {
-                if (m.leaf0) c += dfs_leaf<false>(T, C, r.zc[0], d0, r.val[0], none, 0.f, G);
-                if (m.leaf1) c += dfs_leaf<false>(T, C, r.zc[1], d1, r.val[1], none, 0.f, G);
             }
             tile[m.f * 32 + lane] += c;
         }
@@ -244,15 +267,15 @@ __device__ void dfs_tree(const DfsRec* __restrict__ rec, int64_t nrec, const flo
             // descend into the first internal child; the next record is its
             const int side = m.leaf0 ? 1 : 0;
             dfs_store(stk, k, 0, lane, C);
-            lvl[k] = (int)(i * 2 + side);
-            const bool o = side ? (!gl && oold) : (gl && oold);
-            om = (om & ~(1ull << k)) | ((uint64_t)o << k);
-            gm = (gm & ~(1ull << k)) | ((uint64_t)gl << k);
-            float2 a[4];
-            dfs_factor(T, (side ? r.zc[1] : r.zc[0]), side ? d1 : d0, a);
+            lvl[k] = i * 2 + side;
+            om = dfs_setbit(om, k, (side ? (ol - o0) : o0) != 0.f);
+            gm = dfs_setbit(gm, k, gl);
+            const float zc = side ? r.zc[1] : r.zc[0], d = side ? d1 : d0;
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
-                C[p] = mul2(C[p], rep ? mul2(a[p], R[p]) : a[p]);
+                float2 a = fma2(T[p], f2s(d), f2s(zc));
+                if (rep) a = mul2(a, R[p]);
+                C[p] = mul2(C[p], a);
                 G[p] = f2s(0.f);
             }
             continue;
@@ -267,51 +290,56 @@ __device__ void dfs_tree(const DfsRec* __restrict__ rec, int64_t nrec, const flo
             const DfsRec rp = dfs_load(rec + (L >> 1));
             const DfsMeta mp = dfs_meta(rp);
             const bool repp = mp.anc != (int)kDfsNoAnc;
-            const bool ooldp = repp ? ((om >> mp.anc) & 1ull) != 0 : true;
-            const bool glp = ((gm >> kp) & 1ull) != 0;
+            const float olp = (!repp || dfs_bit(om, mp.anc)) ? 1.f : 0.f;
+            const float o0p = dfs_bit(gm, kp) ? olp : 0.f;
+            const float dp0 = o0p - rp.zc[0], dp1 = (olp - o0p) - rp.zc[1];
+            const float ds = side ? dp1 : dp0, zs = side ? rp.zc[1] : rp.zc[0];
+            const bool sib_leaf = side ? mp.leaf0 : mp.leaf1;
             float2 Cp[4], Gp[4];
-            float2 Rp[4] = {none[0], none[1], none[2], none[3]};
             dfs_fetch(stk, kp, 0, lane, Cp);
             if (side == 1 && !mp.leaf0) {
-                dfs_fetch(stk, kp, 2, lane, Gp);  // left subtree's share, stored before the descent
+                dfs_fetch(stk, kp, 2, lane, Gp);  // the left subtree's share, stored before the descent
             } else {
 #pragma unroll
                 for (int p = 0; p < 4; ++p) Gp[p] = f2s(0.f);
             }
-            float doldp = 0.f;
-            if (repp) {
-                doldp = (ooldp ? 1.f : 0.f) - rp.zold;
+            float c;
+            if (!repp) {
+                if (sib_leaf) {  // the leaf sibling's part of G_parent, recomputed
+                    const float vs = side ? rp.val[0] : rp.val[1];
+                    const float vd = vs * (side ? dp0 : dp1), vz = vs * (side ? rp.zc[0] : rp.zc[1]);
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) Gp[p] = fma2(T[p], f2s(vd), add2(Gp[p], f2s(vz)));
+                }
+                c = ds * dfs_dot(Cp, G);
+#pragma unroll
+                for (int p = 0; p < 4; ++p) Gp[p] = fma2(fma2(T[p], f2s(ds), f2s(zs)), G[p], Gp[p]);
+            } else {
+                const float doldp = olp - rp.zold;
                 dfs_rold(T, rp.zold, doldp, Rp);
-            }
-            const float dp0 = ((glp && ooldp) ? 1.f : 0.f) - rp.zc[0];
-            const float dp1 = ((!glp && ooldp) ? 1.f : 0.f) - rp.zc[1];
-            // the leaf sibling's part of G_parent (not stored: recomputed)
-            const int sib = 1 - side;
-            if (sib == 0 ? mp.leaf0 : mp.leaf1) {
-                float2 fs[4];
-                if (repp) dfs_edge_factor<true>(T, (sib ? rp.zc[1] : rp.zc[0]), sib ? dp1 : dp0, Rp, fs);
-                else dfs_edge_factor<false>(T, (sib ? rp.zc[1] : rp.zc[0]), sib ? dp1 : dp0, Rp, fs);
-                const float2 vs = f2s((sib ? rp.val[1] : rp.val[0]));
+                if (sib_leaf) {
+                    float2 fs[4];
+                    dfs_edge_factor<true>(T, side ? rp.zc[0] : rp.zc[1], side ? dp0 : dp1, Rp, fs);
+                    const float2 vs = f2s(side ? rp.val[0] : rp.val[1]);
 #pragma unroll
-                for (int p = 0; p < 4; ++p) Gp[p] = fma2(fs[p], vs, Gp[p]);
+                    for (int p = 0; p < 4; ++p) Gp[p] = fma2(fs[p], vs, Gp[p]);
+                }
+                float2 factor[4];
+                c = dfs_edge<true>(T, Cp, G, zs, ds, Rp, doldp, factor);
+#pragma unroll
+                for (int p = 0; p < 4; ++p) Gp[p] = fma2(factor[p], G[p], Gp[p]);
             }
-            float2 factor[4];
-            const float c = repp ? dfs_edge<true>(T, Cp, G, (side ? rp.zc[1] : rp.zc[0]), side ? dp1 : dp0, Rp, doldp, factor)
-                                 : dfs_edge<false>(T, Cp, G, (side ? rp.zc[1] : rp.zc[0]), side ? dp1 : dp0, none, 0.f, factor);
             tile[mp.f * 32 + lane] += c;
-#pragma unroll
-            for (int p = 0; p < 4; ++p) Gp[p] = fma2(factor[p], G[p], Gp[p]);
             if (side == 0 && !mp.leaf1) {
                 // visit the right child next (the next record)
                 dfs_store(stk, kp, 2, lane, Gp);
-                lvl[kp] = (L & ~1) | 1;
-                const bool o = !glp && ooldp;
-                om = (om & ~(1ull << kp)) | ((uint64_t)o << kp);
-                float2 a[4];
-                dfs_factor(T, rp.zc[1], dp1, a);
+                lvl[kp] = L | 1;
+                om = dfs_setbit(om, kp, (olp - o0p) != 0.f);
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
-                    C[p] = mul2(Cp[p], repp ? mul2(a[p], Rp[p]) : a[p]);
+                    float2 a = fma2(T[p], f2s(dp1), f2s(rp.zc[1]));
+                    if (repp) a = mul2(a, Rp[p]);
+                    C[p] = mul2(Cp[p], a);
                     G[p] = f2s(0.f);
                 }
                 break;
@@ -356,7 +384,9 @@ __global__ void __launch_bounds__(kDfsMaxWarps * 32) dfs_kernel(DfsArgs a) {
         }
         for (int t = t0; t < t1; ++t) {
             const int64_t b = a.tree_off[t], n = a.tree_off[t + 1] - b;
-            if (n > 0) dfs_tree(a.rec + b, n, xs, tile, stk, lvl, lane, T, W);
+            if (n <= 0) continue;
+            if (a.levels <= 32) dfs_tree<uint32_t>(a.rec + b, (int)n, xs, tile, stk, lvl, lane, T, W);
+            else dfs_tree<uint64_t>(a.rec + b, (int)n, xs, tile, stk, lvl, lane, T, W);
         }
     }
     __syncwarp();
