@@ -72,9 +72,13 @@ def _load():
         lib.orc_sii3_exact.argtypes = [E, vp, i64, i32, vp]
         lib.orc_brute_force3.argtypes = [E, vp, vp]
         lib.orc_alg1_shap.argtypes = [E, vp, i64, i32, i32, vp]
+        lib.orc_sii_order_exact.argtypes = [E, vp, i64, i32, i32, vp]
+        lib.orc_brute_force_order.argtypes = [E, vp, i32, vp]
+        lib.orc_alg1_order.argtypes = [E, vp, i32, i32, vp]
         for f in ("orc_gl_nodes", "orc_shap_exact", "orc_sii_exact", "orc_shap_quad",
                   "orc_brute_force", "orc_alg1", "orc_grad_exact", "orc_path_stats",
-                  "orc_sii3_exact", "orc_brute_force3", "orc_alg1_shap"):
+                  "orc_sii3_exact", "orc_brute_force3", "orc_alg1_shap", "orc_sii_order_exact",
+                  "orc_brute_force_order", "orc_alg1_order"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -229,6 +233,38 @@ def alg1_shap(ens, X, n: int = 8, n_threads: int | None = None) -> np.ndarray:
     _check(_load().orc_alg1_shap(b.ref(), X.ctypes.data, X.shape[0], n, n_threads or threads(),
                                  phi.ctypes.data), "orc_alg1_shap")
     return phi
+
+
+def n_subsets(F: int, s: int) -> int:
+    from math import comb
+
+    return comb(F, s)
+
+
+def sii_order_exact(ens, X, s: int, n_threads: int | None = None) -> np.ndarray:
+    """Order-s SII, M x C(F, s), subsets in lexicographic order."""
+    b = _Bound(ens)
+    X = _f32(X, b.F)
+    out = np.zeros((X.shape[0], n_subsets(b.F, s)))
+    _check(_load().orc_sii_order_exact(b.ref(), X.ctypes.data, X.shape[0], s, n_threads or threads(),
+                                       out.ctypes.data), "orc_sii_order_exact")
+    return out
+
+
+def brute_force_order(ens, x, s: int) -> np.ndarray:
+    b = _Bound(ens)
+    x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1)
+    out = np.zeros(n_subsets(b.F, s))
+    _check(_load().orc_brute_force_order(b.ref(), x.ctypes.data, s, out.ctypes.data), "orc_brute_force_order")
+    return out
+
+
+def alg1_order(ens, x, s: int, n: int) -> np.ndarray:
+    b = _Bound(ens)
+    x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1)
+    out = np.zeros(n_subsets(b.F, s))
+    _check(_load().orc_alg1_order(b.ref(), x.ctypes.data, s, n, out.ctypes.data), "orc_alg1_order")
+    return out
 
 
 def grad_exact(ens, X, grad_phi, leaves=None, n_threads: int | None = None):

@@ -619,8 +619,73 @@ typedef struct {
     double t[256], w[256];
     double *p;   /* live multiplier per feature */
     int *seen;   /* p[f] != UNSEEN, equivalently f in the active set A */
-    double *out; /* order 1: phi[F]; order 2: sii[F*F] */
+    double *out; /* order 1: phi[F]; order 2: sii[F*F]; order 3: F^3; compact: C(F, s) */
+    int compact; /* out is indexed by the lexicographic rank of the sorted s-subset */
 } alg1_ctx;
+
+/* C(n, k) as an exact integer (0 outside 0 <= k <= n). */
+static int64_t n_choose_k(int n, int k) {
+    if (k < 0 || n < k) return 0;
+    int64_t r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+/* Lexicographic rank of the sorted subset c[0] < ... < c[s-1] of {0..F-1}:
+ * the subsets before it are those that agree on c[0..i-1] and have a smaller
+ * i-th element, counted position by position. */
+static int64_t subset_rank(const int *c, int s, int F) {
+    int64_t r = 0;
+    int prev = -1;
+    for (int i = 0; i < s; ++i) {
+        r += n_choose_k(F - prev - 1, s - i) - n_choose_k(F - c[i], s - i);
+        prev = c[i];
+    }
+    return r;
+}
+
+static void sort_ints(int *c, int s) {
+    for (int i = 1; i < s; ++i) {
+        int v = c[i], k = i - 1;
+        while (k >= 0 && c[k] > v) { c[k + 1] = c[k]; --k; }
+        c[k + 1] = v;
+    }
+}
+
+/* Order-s update of one edge on feature f (Alg. 1): every (s-1)-subset P of the
+ * active set without f adds sum_m w_m H_u delta_e prod_{j in P} gamma_j. */
+static void alg1_subsets(alg1_ctx *C, int f, const double *Hu, const double *delta) {
+    const int F = C->F, s = C->order, n = C->n;
+    int act[256], na = 0;
+    for (int j = 0; j < F; ++j)
+        if (j != f && C->seen[j]) act[na++] = j;
+    const int r = s - 1;
+    if (na < r) return;
+    int idx[16];
+    for (int i = 0; i < r; ++i) idx[i] = i;
+    for (;;) {
+        double acc = 0.0;
+        for (int m = 0; m < n; ++m) {
+            double g = C->w[m] * Hu[m] * delta[m];
+            for (int i = 0; i < r; ++i) {
+                double aj = C->p[act[idx[i]]] - 1.0;
+                g *= aj / (1.0 + aj * C->t[m]);
+            }
+            acc += g;
+        }
+        int c[16];
+        for (int i = 0; i < r; ++i) c[i] = act[idx[i]];
+        c[r] = f;
+        sort_ints(c, s);
+        C->out[subset_rank(c, s, F)] += acc;
+        /* next (s-1)-combination of 0..na-1 */
+        int i = r - 1;
+        while (i >= 0 && idx[i] == na - r + i) --i;
+        if (i < 0) break;
+        ++idx[i];
+        for (int k = i + 1; k < r; ++k) idx[k] = idx[k - 1] + 1;
+    }
+}
 
 static void alg1_dfs(alg1_ctx *C, int32_t v, const double *c, double wprod, double *H) {
     const orc_ens *e = C->e;
@@ -661,7 +726,9 @@ static void alg1_dfs(alg1_ctx *C, int32_t v, const double *c, double wprod, doub
         double aup = pup - 1.0;
         for (int m = 0; m < n; ++m)
             delta[m] = ae / (1.0 + ae * C->t[m]) - aup / (1.0 + aup * C->t[m]);
-        if (C->order == 1) {
+        if (C->compact) {
+            alg1_subsets(C, f, Hu, delta);
+        } else if (C->order == 1) {
             double acc = 0.0;
             for (int m = 0; m < n; ++m) acc += C->w[m] * Hu[m] * delta[m];
             C->out[f] += acc;
@@ -728,6 +795,175 @@ int orc_alg1(const orc_ens *e, const float *x, int order, int n, double *out) {
         bias += tree_bias(e, C->base, 0);
     }
     if (order == 1) out[F] = bias;
+    free(C->p);
+    free(C->seen);
+    free(C);
+    return 0;
+}
+
+/* Order-s Shapley interaction index for any s (Thm 1 with |S| = s): per
+ * merged path and s-subset S of its elements,
+ *   SII_S += val prod_{i in S} (o_i - z_i) int_0^1 prod_{j not in S} a_j(p) dp,
+ * integrated exactly (Bernstein form).  Output compact: M x C(F, s), entry
+ * [sample][rank] with rank the lexicographic rank of the sorted feature set. */
+typedef struct {
+    const paths_t *P;
+    const float *X;
+    int64_t s_begin, s_end;
+    int F, s;
+    int64_t n_sub;
+    double *out;
+} ojob_t;
+
+static void *order_exact_worker(void *arg) {
+    ojob_t *J = (ojob_t *)arg;
+    const paths_t *P = J->P;
+    const int F = J->F, s = J->s;
+    int dmax = P->max_d > 0 ? P->max_d : 1;
+    double *o = (double *)malloc(sizeof(double) * dmax);
+    double *zz = (double *)malloc(sizeof(double) * dmax);
+    double *oo = (double *)malloc(sizeof(double) * dmax);
+    double *scr = (double *)malloc(sizeof(double) * 2 * (dmax + 1));
+    int *in = (int *)malloc(sizeof(int) * dmax);
+    for (int64_t sm = J->s_begin; sm < J->s_end; ++sm) {
+        const float *x = J->X + sm * F;
+        double *out = J->out + sm * J->n_sub;
+        for (int64_t q = 0; q < J->n_sub; ++q) out[q] = 0.0;
+        for (int64_t p = 0; p < P->n_paths; ++p) {
+            const ppath *pp = &P->p[p];
+            const pelem *el = P->el + pp->el_begin;
+            const int d = pp->d;
+            if (d < s) continue;
+            for (int j = 0; j < d; ++j) o[j] = satisfied(&el[j], x);
+            int idx[16];
+            for (int i = 0; i < s; ++i) idx[i] = i;
+            for (;;) {
+                for (int j = 0; j < d; ++j) in[j] = 0;
+                double v = pp->val;
+                int c[16];
+                for (int i = 0; i < s; ++i) {
+                    in[idx[i]] = 1;
+                    v *= o[idx[i]] - el[idx[i]].z;
+                    c[i] = el[idx[i]].feat;
+                }
+                int n = 0;
+                for (int l = 0; l < d; ++l) {
+                    if (in[l]) continue;
+                    zz[n] = el[l].z;
+                    oo[n] = o[l];
+                    ++n;
+                }
+                v *= bernstein_integral(zz, oo, n, scr);
+                sort_ints(c, s);
+                out[subset_rank(c, s, F)] += v;
+                int i = s - 1;
+                while (i >= 0 && idx[i] == d - s + i) --i;
+                if (i < 0) break;
+                ++idx[i];
+                for (int k = i + 1; k < s; ++k) idx[k] = idx[k - 1] + 1;
+            }
+        }
+    }
+    free(o); free(zz); free(oo); free(scr); free(in);
+    return NULL;
+}
+
+int orc_sii_order_exact(const orc_ens *e, const float *X, int64_t M, int s, int n_threads, double *out) {
+    const int F = e->n_features;
+    if (s < 1 || s > 16 || s > F) return -1;
+    paths_t P;
+    if (build_paths(e, &P)) return -1;
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > M) n_threads = (int)(M > 0 ? M : 1);
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
+    ojob_t *jobs = (ojob_t *)malloc(sizeof(ojob_t) * (size_t)n_threads);
+    if (!th || !jobs) { free(th); free(jobs); free_paths(&P); return -1; }
+    int64_t per = (M + n_threads - 1) / n_threads;
+    for (int i = 0; i < n_threads; ++i) {
+        jobs[i].P = &P;
+        jobs[i].X = X;
+        jobs[i].F = F;
+        jobs[i].s = s;
+        jobs[i].n_sub = n_choose_k(F, s);
+        jobs[i].out = out;
+        jobs[i].s_begin = i * per < M ? i * per : M;
+        jobs[i].s_end = (i + 1) * per < M ? (i + 1) * per : M;
+        pthread_create(&th[i], NULL, order_exact_worker, &jobs[i]);
+    }
+    for (int i = 0; i < n_threads; ++i) pthread_join(th[i], NULL);
+    free(th);
+    free(jobs);
+    free_paths(&P);
+    return 0;
+}
+
+/* Order-s SII for one sample by subset enumeration (App. C):
+ *   SII_S = sum_{T subset of [F] \ S} |T|! (F - |T| - s)! / (F - s + 1)! Delta_S f(T),
+ *   Delta_S f(T) = sum_{L subset of S} (-1)^(s - |L|) f(T + L).
+ * Compact output C(F, s); needs s <= F <= 16. */
+int orc_brute_force_order(const orc_ens *e, const float *x, int s, double *out) {
+    const int F = e->n_features;
+    if (s < 1 || s > F || F > 16) return -1;
+    uint32_t NS = 1u << F;
+    double *fs = (double *)malloc(sizeof(double) * NS);
+    if (!fs) return -1;
+    for (uint32_t S = 0; S < NS; ++S) {
+        double acc = 0.0;
+        for (int t = 0; t < e->n_trees; ++t) acc += game(e, e->node_offsets[t], 0, x, S);
+        fs[S] = acc;
+    }
+    double fact[40];
+    fact[0] = 1.0;
+    for (int k = 1; k < 40; ++k) fact[k] = fact[k - 1] * (double)k;
+    int idx[16];
+    for (int i = 0; i < s; ++i) idx[i] = i;
+    int64_t rank = 0;
+    for (;;) {
+        uint32_t mS = 0;
+        for (int i = 0; i < s; ++i) mS |= 1u << idx[i];
+        double sii = 0.0;
+        for (uint32_t T = 0; T < NS; ++T) {
+            if (T & mS) continue;
+            int t = __builtin_popcount(T);
+            double wgt = fact[t] * fact[F - t - s] / fact[F - s + 1];
+            double delta = 0.0;
+            for (uint32_t L = mS;; L = (L - 1) & mS) {
+                int l = __builtin_popcount(L);
+                delta += ((s - l) % 2 ? -1.0 : 1.0) * fs[T | L];
+                if (L == 0) break;
+            }
+            sii += wgt * delta;
+        }
+        out[rank++] = sii;  /* combinations are visited in lexicographic order */
+        int i = s - 1;
+        while (i >= 0 && idx[i] == F - s + i) --i;
+        if (i < 0) break;
+        ++idx[i];
+        for (int k = i + 1; k < s; ++k) idx[k] = idx[k - 1] + 1;
+    }
+    free(fs);
+    return 0;
+}
+
+/* Algorithm 1 for any order s on one sample with n points; compact output
+ * C(F, s) in lexicographic order. */
+int orc_alg1_order(const orc_ens *e, const float *x, int s, int n, double *out) {
+    const int F = e->n_features;
+    if (s < 1 || s > 16 || s > F) return -1;
+    alg1_ctx *C = (alg1_ctx *)calloc(1, sizeof(alg1_ctx));
+    if (!C) return -1;
+    if (orc_gl_nodes(n, C->t, C->w)) { free(C); return -1; }
+    C->e = e; C->x = x; C->order = s; C->n = n; C->F = F; C->out = out; C->compact = 1;
+    C->p = (double *)calloc((size_t)F, sizeof(double));
+    C->seen = (int *)calloc((size_t)F, sizeof(int));
+    const int64_t nout = n_choose_k(F, s);
+    for (int64_t k = 0; k < nout; ++k) out[k] = 0.0;
+    double ones[256], H[256];
+    for (int m = 0; m < n; ++m) ones[m] = 1.0;
+    for (int t = 0; t < e->n_trees; ++t) {
+        C->base = e->node_offsets[t];
+        if (e->left[C->base] >= 0) alg1_dfs(C, 0, ones, 1.0, H);
+    }
     free(C->p);
     free(C->seen);
     free(C);

@@ -18,6 +18,9 @@
  *   orc_brute_force3    SII_ijk by subset enumeration.
  *   orc_alg1            Algorithm 1 (DFS with telescoping, orders 1, 2 and 3).
  *   orc_alg1_shap       Algorithm 1, first order, many samples on threads.
+ *   orc_sii_order_exact order-s SII (any s) by the exact expansion (Thm 1).
+ *   orc_brute_force_order  order-s SII by subset enumeration (App. C).
+ *   orc_alg1_order      Algorithm 1 for any order s.
  *   orc_grad_exact      d(sum grad_phi*phi)/d(leaf values) and /d(edge weights),
  *                       differentiating Thm 1 analytically (no paper passage;
  *                       pinned by finite differences of the brute force).
@@ -83,6 +86,14 @@ int orc_brute_force3(const orc_ens *e, const float *x, double *sii3);
  * (F+1 incl. E[f]), order 2 fills sii (F x F, symmetric, zero diagonal),
  * order 3 fills F x F x F (symmetric, zero where indices coincide). */
 int orc_alg1(const orc_ens *e, const float *x, int order, int n, double *out);
+
+/* Order-s SII for any 1 <= s <= min(F, 16), compact: entry [sample][rank] with
+ * rank the lexicographic rank of the sorted feature set among the C(F, s)
+ * subsets.  Exact expansion (M samples), subset enumeration (one sample,
+ * F <= 16) and Algorithm 1 with n points (one sample). */
+int orc_sii_order_exact(const orc_ens *e, const float *X, int64_t M, int s, int n_threads, double *out);
+int orc_brute_force_order(const orc_ens *e, const float *x, int s, double *out);
+int orc_alg1_order(const orc_ens *e, const float *x, int s, int n, double *out);
 
 /* Algorithm 1, first order, for M samples (phi: M x (F+1) incl. E[f]),
  * threaded over samples: the paper's CPU quadrature method as a baseline. */

@@ -371,3 +371,66 @@ def test_categorical_exact_equals_brute_force(seed):
     assert np.allclose(ex_phi.sum(axis=1), oracle.predict(ens, X), atol=1e-12)
     a1 = np.stack([oracle.alg1(ens, X[s], 1, 8) for s in range(X.shape[0])])
     assert np.allclose(a1, ex_phi, atol=1e-12)
+
+
+# ------------------------------------------------------------ any order
+
+def _dense_to_compact(dense, F, s):
+    import itertools
+
+    return np.array([dense[c] for c in itertools.combinations(range(F), s)])
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_any_order_exact_equals_brute_force(seed):
+    """Thm 1 with |S| = s integrated exactly against subset enumeration with the
+    order-s weights of App. C, s = 1..6, repeated features included; the
+    brute force writes subsets in enumeration order and the expansion by the
+    rank formula, so agreement also pins the compact layout."""
+    ens = tiny_ensemble(2400 + seed, n_trees=3, depth=9, F=7, n_train=3000)
+    X = synth.normal(2400 + seed, 1, (3, 7))
+    for s in range(1, 7):
+        ex = oracle.sii_order_exact(ens, X, s)
+        for r in range(X.shape[0]):
+            bf = oracle.brute_force_order(ens, X[r], s)
+            scale = max(1.0, np.abs(bf).max())
+            assert np.abs(ex[r] - bf).max() < 1e-12 * scale, (s, r)
+
+
+def test_any_order_reduces_to_orders_one_to_three():
+    ens = tiny_ensemble(2450, n_trees=3, depth=8, F=6, n_train=2000)
+    X = synth.normal(2450, 1, (4, 6))
+    phi = oracle.shap_exact(ens, X)
+    sii2, _ = oracle.sii_exact(ens, X)
+    sii3 = oracle.sii3_exact(ens, X)
+    o1 = oracle.sii_order_exact(ens, X, 1)
+    o2 = oracle.sii_order_exact(ens, X, 2)
+    o3 = oracle.sii_order_exact(ens, X, 3)
+    for r in range(4):
+        assert np.allclose(o1[r], phi[r, :6], atol=1e-14)
+        assert np.allclose(o2[r], _dense_to_compact(sii2[r], 6, 2), atol=1e-14)
+        assert np.allclose(o3[r], _dense_to_compact(sii3[r], 6, 3), atol=1e-14)
+
+
+@pytest.mark.parametrize("s", [4, 5])
+def test_any_order_alg1_exact_at_theorem2_bound(s):
+    """Algorithm 1 of order s with n = ceil((d - s + 1)/2) points is exact (Thm 2)."""
+    ens = tiny_ensemble(2500 + s, n_trees=3, depth=10, F=8, n_train=4000)
+    _, dmax, _ = oracle.path_stats(ens)
+    X = synth.normal(2500 + s, 1, (3, 8))
+    n = max(1, math.ceil((dmax - s + 1) / 2))
+    ref = oracle.sii_order_exact(ens, X, s)
+    for r in range(3):
+        got = oracle.alg1_order(ens, X[r], s, n)
+        assert np.abs(got - ref[r]).max() < 1e-12 * max(1.0, np.abs(ref[r]).max())
+
+
+def test_any_order_golden_chain():
+    """The hand-derived third-order value of the three-feature chain, and the
+    closed form for s = d: a path whose every feature is in S contributes
+    val prod (o_i - z_i) (the integral of the empty product is 1)."""
+    spec, ens = [g for g in golden_trees() if g[0]["name"] == "three_feature_chain"][0]
+    x = sample_x(spec["samples"][0])
+    for fn in (lambda: oracle.sii_order_exact(ens, x[None], 3)[0], lambda: oracle.brute_force_order(ens, x, 3),
+               lambda: oracle.alg1_order(ens, x, 3, 8)):
+        assert abs(fn()[0] - spec["samples"][0]["sii012"]) < 1e-15
