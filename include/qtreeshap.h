@@ -202,6 +202,24 @@ qts_status qts_shap_interactions3(qts_ensemble *ens, const float *X, int64_t M, 
                                   int32_t n_quad, float *sii3, qts_stream_t stream);
 
 /*
+ * qts_shap_interactions_order - Shapley interaction indices of any order s,
+ * 2 <= s <= 8 (Thm 1 with |S| = s; Alg. 1 with general s; the paper times
+ * orders 2-6, Sec. 8).  For every merged path containing all features of S,
+ *     SII_S += val prod_{i in S} (o_i - z_i) int_0^1 prod_{j not in S} a_j(p) dp,
+ * integrated with n_quad Gauss-Legendre points (exact when the path has at most
+ * 2 n_quad + s - 1 unique features, Thm 2).  Output, compact:
+ *   out    device, M x C(F, s) fp32, overwritten; entry [sample][rank] for the
+ *          features a_1 < ... < a_s, rank = their lexicographic rank among the
+ *          C(F, s) subsets (s = 3 gives the layout of qts_shap_interactions3)
+ * Cross-path accumulation is FP64 in the ensemble's workspace (C(F, s) * M
+ * doubles, grown on demand with cudaMalloc).  Paths of at most 16 unique
+ * features, FP32 tables only; QTS_ERR_ARG for s outside [2, 8],
+ * QTS_ERR_UNSUPPORTED beyond those limits or when C(F, s) * M > 2^40.
+ */
+qts_status qts_shap_interactions_order(qts_ensemble *ens, const float *X, int64_t M, int32_t F,
+                                       int32_t order, int32_t n_quad, float *out, qts_stream_t stream);
+
+/*
  * qts_shap_interactions_noalloc - qts_shap_interactions without any device
  * allocation.  No counterpart in the paper: this is for callers that must not
  * allocate device memory during the call - code running while a CUDA stream is

@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "QTS_OK", 1: "QTS_ERR_ARG", 2: "QTS_ERR_CUDA", 3: "QTS_ERR_OO
 # every symbol include/qtreeshap.h declares
 EXPORTS = ("qts_load_ensemble", "qts_load_ensemble_cat", "qts_update_params", "qts_shap_values", "qts_shap_values_alg1",
            "qts_shap_interactions",
-           "qts_shap_interactions_noalloc", "qts_shap_interactions3",
+           "qts_shap_interactions_noalloc", "qts_shap_interactions3", "qts_shap_interactions_order",
            "qts_shap_backward", "qts_batched_fwd_bwd", "qts_autotune", "qts_sync_status",
            "qts_get_info", "qts_describe_ensemble", "qts_batched_kernel_count", "qts_batched_last_kernel_ms", "qts_gauss_legendre", "qts_last_error",
            "qts_free")
@@ -75,6 +75,7 @@ def lib():
         L.qts_shap_interactions.argtypes = [vp, vp, i64, i32, i32, vp, vp]
         L.qts_shap_interactions_noalloc.argtypes = [vp, vp, i64, i32, i32, vp, vp]
         L.qts_shap_interactions3.argtypes = [vp, vp, i64, i32, i32, vp, vp]
+        L.qts_shap_interactions_order.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp]
         L.qts_shap_backward.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, vp]
         L.qts_batched_fwd_bwd.argtypes = [i32, vp, i32, vp]
         L.qts_autotune.argtypes = [vp, vp, i64, i32, ctypes.c_char_p, vp]
@@ -284,6 +285,22 @@ def shap_interactions3(ens: Ensemble, X, n_quad: int = 8, out=None, stream=None)
     if out is None:
         out = torch.empty((M, comb(F, 3)), dtype=torch.float32, device=X.device)
     _check(lib().qts_shap_interactions3(ens.handle, _ptr(X), M, F, n_quad, _ptr(out), _stream(stream)))
+    return out
+
+
+def shap_interactions_order(ens: Ensemble, X, order: int, n_quad: int = 8, out=None, stream=None):
+    """M x C(F, order) float32: SII of every feature subset of size `order`,
+    subsets in lexicographic order (itertools.combinations(range(F), order))."""
+    import math
+
+    import torch
+
+    _check_x(ens, X)
+    M, F = X.shape
+    if out is None:
+        out = torch.empty((M, math.comb(F, order)), dtype=torch.float32, device=X.device)
+    _check(lib().qts_shap_interactions_order(ens.handle, _ptr(X), M, F, order, n_quad, _ptr(out),
+                                             _stream(stream)))
     return out
 
 
