@@ -22,6 +22,7 @@ namespace qts {
 constexpr int kIntkWarps = 4;
 constexpr int kIntkMaxD = 16;
 constexpr int kIntkMaxOrder = 8;
+constexpr int kIntkPairs = 4;  // node pairs per pass: all 8 nodes, one atomic per subset
 
 // C(n, R) for a compile-time R; 0 when n < R.
 template <int R>
@@ -60,9 +61,9 @@ struct IntkArgs {
 struct IntkPath {
     const Rec32* r;     // the path's records (header, elements) in shared memory
     const float* dd;    // [element][32] d = o - z of the lane's sample
-    const float2* S;    // [element][32] suffix products of the current node pair
+    const float2* S;    // [element][pair][32] suffix products at this pass's nodes
     const int* fe;      // [element] feature (warp-uniform)
-    float2 T;           // the node pair
+    float2 T[kIntkPairs];  // this pass's nodes
     int nreal;          // elements with a real feature (padding excluded)
     int F;
     int lane;
@@ -75,8 +76,11 @@ struct IntkPath {
 // the product of the unchosen elements before `start` (times w val), dp the
 // product of the chosen elements' d, rank the lexicographic rank so far.
 template <int REM>
-__device__ __forceinline__ void intk_choose(const IntkPath& c, int start, float2 R, float dp, int64_t rank,
-                                            int prev) {
+__device__ __forceinline__ void intk_choose(const IntkPath& c, int start, const float2 (&R0)[kIntkPairs],
+                                            float dp, int64_t rank, int prev) {
+    float2 R[kIntkPairs];
+#pragma unroll
+    for (int k = 0; k < kIntkPairs; ++k) R[k] = R0[k];
 #pragma unroll 1
     for (int j = start; j + REM < c.nreal; ++j) {
         const int f = c.fe[j];
@@ -84,13 +88,18 @@ __device__ __forceinline__ void intk_choose(const IntkPath& c, int start, float2
         // subsets that agree so far and take a smaller feature here come first
         const int64_t rk = rank + binom_r<REM + 1>(c.F - prev - 1) - binom_r<REM + 1>(c.F - f);
         if constexpr (REM == 0) {
-            const float2 t = mul2(R, c.S[j * 32 + c.lane]);
+            const float2* Sj = c.S + (size_t)j * kIntkPairs * 32 + c.lane;
+            float2 t = mul2(R[0], Sj[0]);
+#pragma unroll
+            for (int k = 1; k < kIntkPairs; ++k) t = fma2(R[k], Sj[k * 32], t);
             const float v = (t.x + t.y) * dp * d;
             if (c.live && v != 0.f) atomicAdd(&c.acc[rk * c.M + c.s], (double)v);
         } else {
             intk_choose<REM - 1>(c, j + 1, R, dp * d, rk, f);
         }
-        R = mul2(R, fma2(c.T, f2s(d), f2s(c.r[1 + j].z)));  // element j stays unchosen from here on
+        const float2 z2 = f2s(c.r[1 + j].z), d2 = f2s(d);
+#pragma unroll
+        for (int k = 0; k < kIntkPairs; ++k) R[k] = mul2(R[k], fma2(c.T[k], d2, z2));  // j stays unchosen
     }
 }
 
@@ -110,18 +119,26 @@ __device__ __forceinline__ void intk_path(const Rec32* __restrict__ r, const flo
     }
     __syncwarp();
     if (nreal >= a.order) {
-        IntkPath c{r, dd, S, fe, f2s(0.f), nreal, F, lane, s < a.M, s, a.M, a.acc};
+        IntkPath c{r, dd, S, fe, {}, nreal, F, lane, s < a.M, s, a.M, a.acc};
         const float val = r[0].z;
-        for (int m = 0; m < a.q.n_pad; m += 2) {
-            c.T = f2(a.q.t[m], a.q.t[m + 1]);
-            // suffix products S_j = prod_{l > j} a_l at this node pair
-            float2 suf = f2s(1.f);
+        for (int m0 = 0; m0 < a.q.n_pad; m0 += 2 * kIntkPairs) {
+            float2 R0[kIntkPairs], suf[kIntkPairs];
+#pragma unroll
+            for (int k = 0; k < kIntkPairs; ++k) {
+                c.T[k] = f2(a.q.t[m0 + 2 * k], a.q.t[m0 + 2 * k + 1]);
+                R0[k] = f2(a.q.w[m0 + 2 * k] * val, a.q.w[m0 + 2 * k + 1] * val);
+                suf[k] = f2s(1.f);
+            }
+            // suffix products S_j = prod_{l > j} a_l at this pass's nodes
 #pragma unroll
             for (int j = D - 1; j >= 0; --j) {
-                S[j * 32 + lane] = suf;
-                suf = mul2(suf, fma2(c.T, f2s(dd[j * 32 + lane]), f2s(r[1 + j].z)));
+                const float2 z2 = f2s(r[1 + j].z), d2 = f2s(dd[j * 32 + lane]);
+#pragma unroll
+                for (int k = 0; k < kIntkPairs; ++k) {
+                    S[((size_t)j * kIntkPairs + k) * 32 + lane] = suf[k];
+                    suf[k] = mul2(suf[k], fma2(c.T[k], d2, z2));
+                }
             }
-            const float2 R0 = f2(a.q.w[m] * val, a.q.w[m + 1] * val);
             switch (a.order) {
                 case 2: intk_choose<1>(c, 0, R0, 1.f, 0, -1); break;
                 case 3: intk_choose<2>(c, 0, R0, 1.f, 0, -1); break;
@@ -149,7 +166,7 @@ __host__ __device__ __forceinline__ size_t align16(size_t v) { return (v + 15) &
 __host__ __device__ __forceinline__ IntkSmem intk_smem(int F, int sub, int D) {
     IntkSmem L;
     L.S = 0;
-    L.dd = align16(L.S + (size_t)kIntkWarps * kIntkMaxD * 32 * sizeof(float2));
+    L.dd = align16(L.S + (size_t)kIntkWarps * kIntkMaxD * kIntkPairs * 32 * sizeof(float2));
     L.fe = align16(L.dd + (size_t)kIntkWarps * kIntkMaxD * 32 * sizeof(float));
     L.xs = align16(L.fe + (size_t)kIntkWarps * kIntkMaxD * sizeof(int));
     L.st = align16(L.xs + (size_t)(F + 1) * kTileLd * sizeof(float));
@@ -186,7 +203,7 @@ __global__ void __launch_bounds__(kIntkWarps * 32) intk_kernel(IntkArgs a) {
     }
     const bool has_nan = load_tile_t(xs, a.X, s0, a.M, F, F, 1) || a.cat != 0;
     const int64_t s = s0 + lane;
-    float2* S = S_all + (size_t)warp * kIntkMaxD * 32;
+    float2* S = S_all + (size_t)warp * kIntkMaxD * kIntkPairs * 32;
     float* dd = dd_all + (size_t)warp * kIntkMaxD * 32;
     int* fe = fe_all + (size_t)warp * kIntkMaxD;
     (void)stream_paths<Rec32, D>(a.rec, p0, p1, a.sub, st0, st1, bars, s_phase, &s_flag, a.status,

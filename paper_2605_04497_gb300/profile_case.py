@@ -15,6 +15,8 @@ Cases (synthetic inputs from `synth`):
                      model (1,000 trees, depth 16, F = 14, ~610 leaves per tree), 1,000 rows
   forward-deep20     qts_shap_values on 200 unbalanced trees of depth <= 20 over F = 24
                      (repeated features merged), M = 5,000
+  orders-covtypelike qts_shap_interactions_order on 800 trees of depth 16 over F = 54 (a
+                     CovType-large-shaped stand-in): orders 2-6 for 1 row, 2-4 for 64
   alg1-xgb, alg1-deep20, alg1-adultlike
                      qts_shap_values_alg1 (depth-first form) on the same inputs as
                      forward-xgb, forward-deep20 and forward-adultlike
@@ -45,9 +47,11 @@ def main():
     ap.add_argument("case", choices=["forward-xgb", "adjoint-xgb", "interactions-500", "fused-xgb",
                                      "fused-deep", "adjoint-deep", "interactions3-500",
                                      "forward-adultlike", "forward-deep20", "alg1-xgb", "alg1-deep20",
-                                     "alg1-adultlike"])
+                                     "alg1-adultlike", "orders-covtypelike"])
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
+    if args.case == "orders-covtypelike":
+        return orders_case(args.reps)
     if args.case.endswith("-deep"):
         seed = synth.SEED_BASE + 4
         trees, depth, feats, samples = synth.batch_draw(seed, 64)
@@ -108,6 +112,43 @@ def main():
     print(f"{args.case}: paths {info['n_paths']}, buckets {info['buckets']}")
     print(f"{args.case}: {ms:.3f} ms/call, {w.M * w.ens.n_trees / ms * 1e3:.3e} sample*trees/s"
           + (f", {work / ms / 1e9:.2f} Tops/s algorithmic" if ops else ""))
+    E.close()
+
+
+def orders_case(reps):
+    """Interactions of orders 2-6 on a stand-in for the paper's CovType-large
+    model (Table 1: depth 16, F = 54, up to 14 unique features per path), with
+    800 trees instead of 8,000, for one explained row (as in Table 4; orders
+    2-6) and for 64 rows (orders 2-4)."""
+    import math
+
+    import torch
+
+    import synth
+    import paper_2605_04497_gb300 as qts
+
+    seed = synth.SEED_BASE + 101
+    ens = synth.grow(seed, 800, 16, 54, 20000, 0.1, min_rows=5)
+    E = qts.Ensemble.from_arrays(ens)
+    info = E.info()
+    print(f"orders-covtypelike: {ens.n_trees} trees, paths {info['n_paths']}, max unique {info['max_unique']}")
+    X = torch.from_numpy(synth.normal(seed, synth.STREAM_X, (64, 54))).cuda()
+    for rows, orders in ((1, range(2, 7)), (64, range(2, 5))):
+        for order in orders:
+            fn = lambda: qts.shap_interactions_order(E, X[:rows], order)
+            fn()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn()
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            E.sync_status()
+            print(f"orders-covtypelike: rows {rows}, order {order}: {float(np.median(ts)):.3f} ms/call, "
+                  f"{math.comb(54, order)} subsets per row")
     E.close()
 
 
