@@ -77,3 +77,37 @@ def categorical_ensemble(seed, n_trees=3, depth=7, F=5, cat_features=(0, 2), n_c
     left sets over n_categories), depth > F so features repeat on paths."""
     base = synth.grow(seed, n_trees, depth, F, n_train, 1.0, min_rows=2)
     return synth.make_categorical(base, cat_features, n_categories, seed + 1)
+
+
+def caterpillar_ensemble(seed, depths, F):
+    """One tree per entry of `depths`: every internal node has one leaf child
+    and splits on a feature not used above it, so the longest path has
+    `depth` unique features (the widest merged paths the library takes).
+    Thresholds ~ N(0, 0.5), child weights w and 1 - w with w ~ U(0.2, 0.8),
+    leaf values ~ N(0, 1), random default directions."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for depth in depths:
+        n = 2 * depth + 1
+        left = np.full(n, -1, np.int32)
+        right = np.full(n, -1, np.int32)
+        feature = np.zeros(n, np.int32)
+        thr = np.zeros(n, np.float32)
+        z = np.ones(n, np.float32)
+        val = np.zeros(n, np.float32)
+        defl = rng.integers(0, 2, n).astype(np.uint8)
+        feats = rng.permutation(F)[:depth]
+        for k in range(depth):
+            leaf = depth + 1 + k
+            nxt = k + 1 if k + 1 < depth else depth  # the last internal node has two leaves
+            a, b = (nxt, leaf) if rng.random() < 0.5 else (leaf, nxt)
+            left[k], right[k] = a, b
+            feature[k] = feats[k]
+            thr[k] = rng.normal(0.0, 0.5)
+            w = rng.uniform(0.2, 0.8)
+            z[a], z[b] = w, 1.0 - w
+        for v in range(n):
+            if left[v] < 0:
+                val[v] = rng.normal()
+        parts.append(synth.Ensemble([0, n], left, right, feature, thr, defl, z, val, np.ones(n), F))
+    return synth.concat(parts)
