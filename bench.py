@@ -38,8 +38,8 @@ N_QUAD = 8
 # dram__bytes_read.sum,dram__bytes_write.sum` on `bench.py --steps 1 --warmup 1`
 # (profiles/batch_kernel_dram_batch64.md); valid only while the kernel sources
 # hash to TRAFFIC_HASH, otherwise reported as null.
-TRAFFIC_BYTES = (1.685 + 0.801 + 12.497 + 4.983 + 11.345 + 3.828) * 1e9
-TRAFFIC_HASH = "00a0e9586a03b9ad"
+TRAFFIC_BYTES = (1.684 + 0.799 + 12.541 + 4.953 + 11.343 + 3.827) * 1e9
+TRAFFIC_HASH = "f43243ce70c89602"
 KERNEL_SOURCES = ("qts_batch.cu", "qts_paths.cuh", "qts_device.cuh", "qts_internal.h")
 # FP32-pipe operations per (sample, merged path element, quadrature node)
 OPS_FUSED = 11   # forward + adjoint in one pass

@@ -326,6 +326,16 @@ qts_status qts_describe_ensemble(int32_t n_trees, const int64_t *tree_node_offse
                                  const float *z, const float *leaf_value, int32_t n_features,
                                  uint32_t flags, qts_info *out);
 
+/*
+ * qts_selftest_wait_timeout - exercise the device failure path (no counterpart
+ * in the paper).  Enqueues one block on `stream` that waits, with the same
+ * bounded wait the kernels use for their bulk copies, on a barrier that nothing
+ * completes; after about a second the wait gives up and latches
+ * QTS_ERR_TIMEOUT in the ensemble's status word, which the next
+ * qts_sync_status returns (and clears).  The context stays usable.
+ */
+qts_status qts_selftest_wait_timeout(qts_ensemble *ens, qts_stream_t stream);
+
 /* Gauss-Legendre nodes/weights on [0,1] used by the kernels (fp64, ascending). */
 qts_status qts_gauss_legendre(int32_t n, double *t, double *w);
 

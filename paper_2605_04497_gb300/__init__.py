@@ -26,7 +26,7 @@ EXPORTS = ("qts_load_ensemble", "qts_load_ensemble_cat", "qts_update_params", "q
            "qts_shap_interactions",
            "qts_shap_interactions_noalloc", "qts_shap_interactions3", "qts_shap_interactions_order",
            "qts_shap_backward", "qts_batched_fwd_bwd", "qts_autotune", "qts_sync_status",
-           "qts_get_info", "qts_describe_ensemble", "qts_batched_kernel_count", "qts_batched_last_kernel_ms", "qts_gauss_legendre", "qts_last_error",
+           "qts_get_info", "qts_describe_ensemble", "qts_selftest_wait_timeout", "qts_batched_kernel_count", "qts_batched_last_kernel_ms", "qts_gauss_legendre", "qts_last_error",
            "qts_free")
 
 _lib = None
@@ -80,6 +80,7 @@ def lib():
         L.qts_batched_fwd_bwd.argtypes = [i32, vp, i32, vp]
         L.qts_autotune.argtypes = [vp, vp, i64, i32, ctypes.c_char_p, vp]
         L.qts_sync_status.argtypes = [vp, vp]
+        L.qts_selftest_wait_timeout.argtypes = [vp, vp]
         L.qts_get_info.argtypes = [vp, ctypes.POINTER(QtsInfo)]
         L.qts_describe_ensemble.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, u32,
                                             ctypes.POINTER(QtsInfo)]
@@ -194,6 +195,11 @@ class Ensemble:
 
     def sync_status(self, stream=None):
         _check(lib().qts_sync_status(self.handle, _stream(stream)))
+
+    def selftest_wait_timeout(self, stream=None):
+        """Enqueue a bounded wait that runs out (about a second); the next
+        sync_status raises QtsError with QTS_ERR_TIMEOUT."""
+        _check(lib().qts_selftest_wait_timeout(self.handle, _stream(stream)))
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:

@@ -4,6 +4,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "qts_device.cuh"
 #include "qts_internal.h"
 
 namespace qts {
@@ -128,6 +129,24 @@ qts_status ensure_workspace(qts_ensemble* e, size_t bytes) {
     if (err != cudaSuccess) return cuda_fail(err, "workspace allocation");
     e->work_bytes = want;
     return QTS_OK;
+}
+
+// The device failure path on demand: one block waits, bounded, on an mbarrier
+// that nothing arrives at; the wait runs out and latches QTS_ERR_TIMEOUT in the
+// status word.  No copy is issued, so nothing is left in flight.
+__global__ void wait_selftest_kernel(int* status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0)) report(status, QTS_ERR_TIMEOUT);
+}
+
+cudaError_t launch_wait_selftest(int* status, cudaStream_t st) {
+    wait_selftest_kernel<<<1, 32, 0, st>>>(status);
+    return cudaGetLastError();
 }
 
 qts_status check_call(qts_ensemble* e, const float* X, int64_t M, int32_t F, int32_t n_quad) {
@@ -279,6 +298,13 @@ qts_status qts_shap_values(qts_ensemble* e, const float* X, int64_t M, int32_t F
         ce = launch_fwd_bucket(e, b, X, M, F, qf, qd, phi, e->tune[b.D], s);
         if (ce != cudaSuccess) return cuda_fail(ce, "forward kernel launch");
     }
+    return QTS_OK;
+}
+
+qts_status qts_selftest_wait_timeout(qts_ensemble* e, qts_stream_t stream) {
+    if (!e) return fail(QTS_ERR_ARG, "ensemble handle is NULL");
+    cudaError_t ce = launch_wait_selftest(e->d_status, (cudaStream_t)stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "self-test launch");
     return QTS_OK;
 }
 

@@ -15,8 +15,10 @@ namespace qts {
 // walk (fixed sample, consecutive rows) conflict-free as well.
 constexpr int kTileLd = 33;
 
-// Upper bound on mbarrier polls before a wait is declared failed (each
-// try_wait already suspends for a hardware-defined interval).
+// A wait is declared failed after about kWaitNs of GPU time (the global
+// nanosecond timer), or after kWaitLimit polls as a backstop (each try_wait
+// may suspend for a hardware-defined interval).
+constexpr uint64_t kWaitNs = 1000000000ull;
 constexpr uint32_t kWaitLimit = 1u << 24;
 
 // ------------------------------------------------------------ f32x2 ------
@@ -59,10 +61,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: true when the phase completed; false after kWaitLimit polls.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: true when the phase completed; false once about a second has
+// passed (or kWaitLimit polls), so a copy that never lands ends as a status
+// code instead of a hung context.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (uint32_t it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0; it < kWaitLimit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 63u && global_ns() - t0 > kWaitNs) return false;
+    }
     return false;
 }
 

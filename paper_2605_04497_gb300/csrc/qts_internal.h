@@ -171,6 +171,7 @@ qts_status check_call(qts_ensemble* e, const float* X, int64_t M, int32_t F, int
 // (defined in the .cu files; all enqueue on `st` and return cudaGetLastError)
 
 cudaError_t launch_phi_init(double* phi, int64_t M, int F, double bias, cudaStream_t st);
+cudaError_t launch_wait_selftest(int* status, cudaStream_t st);
 cudaError_t launch_fwd_bucket(const qts_ensemble* e, const Bucket& b, const float* X, int64_t M,
                               int F, const QuadF& q, const QuadD& qd, double* phi, const Tune& tn,
                               cudaStream_t st);
