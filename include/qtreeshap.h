@@ -31,7 +31,7 @@
  *     the ensemble's workspace); enqueue them on one stream.
  *   - X is M x F row-major fp32 with F equal to the ensemble's n_features.
  *     x[f] < threshold goes left, x[f] >= threshold right, NaN goes the node's
- *     default direction.
+ *     default direction (categorical splits: see qts_load_ensemble_cat).
  */
 #ifndef QTREESHAP_H
 #define QTREESHAP_H
