@@ -434,3 +434,48 @@ def test_any_order_golden_chain():
     for fn in (lambda: oracle.sii_order_exact(ens, x[None], 3)[0], lambda: oracle.brute_force_order(ens, x, 3),
                lambda: oracle.alg1_order(ens, x, 3, 8)):
         assert abs(fn()[0] - spec["samples"][0]["sii012"]) < 1e-15
+
+
+@pytest.mark.parametrize("s", [4, 5, 6])
+def test_any_order_closed_form_on_a_caterpillar(s):
+    """A caterpillar tree of depth s (one leaf child per internal node, a new
+    feature at every level): only its two deepest leaves use all s features, so
+    SII over those features is the integral of an empty product (= 1) times
+    val prod_i (o_i - z_i) summed over those two leaves (Thm 1), computed here
+    from the tree arrays."""
+    from helpers import caterpillar_ensemble
+
+    ens = caterpillar_ensemble(3200 + s, [s], s + 2)
+    X = synth.normal(3200 + s, 1, (5, s + 2))
+    feats = sorted(int(f) for f in ens.feature[:s])
+    import itertools
+
+    rank = list(itertools.combinations(range(s + 2), s)).index(tuple(feats))
+    for r in range(X.shape[0]):
+        x = X[r]
+        want = 0.0
+        for leaf in (v for v in range(ens.n_nodes) if ens.left[v] < 0):
+            # walk down from the root to this leaf, collecting (o - z) per level
+            path, v, ok = [], 0, False
+            while ens.left[v] >= 0:
+                for c in (int(ens.left[v]), int(ens.right[v])):
+                    if c == leaf or (ens.left[c] >= 0 and _reaches(ens, c, leaf)):
+                        goes_left = c == ens.left[v]
+                        o = float((x[ens.feature[v]] < ens.threshold[v]) == goes_left)
+                        path.append(o - float(ens.z[c]))
+                        v = c
+                        break
+            if len(path) == s:
+                want += float(ens.leaf_value[leaf]) * float(np.prod(path))
+        got = (oracle.sii_order_exact(ens, x[None], s)[0][rank], oracle.brute_force_order(ens, x, s)[rank],
+               oracle.alg1_order(ens, x, s, 8)[rank])
+        for g in got:
+            assert abs(g - want) < 1e-13 * max(1.0, abs(want)), (s, r, g, want)
+
+
+def _reaches(ens, v, target):
+    if v == target:
+        return True
+    if ens.left[v] < 0:
+        return False
+    return _reaches(ens, int(ens.left[v]), target) or _reaches(ens, int(ens.right[v]), target)
