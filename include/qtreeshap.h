@@ -336,6 +336,35 @@ qts_status qts_describe_ensemble(int32_t n_trees, const int64_t *tree_node_offse
  */
 qts_status qts_selftest_wait_timeout(qts_ensemble *ens, qts_stream_t stream);
 
+/*
+ * qts_describe_paths - host-only: the FP32 path tables that
+ * qts_load_ensemble_cat would upload (Sec. 2: paths merged per feature,
+ * Eq. q_def; bucketed by width), for inspection and tests.  No device memory is
+ * touched.  Call once with records == NULL to get *n_records and *n_paths, then
+ * again with buffers of those sizes.
+ *   records     host, n_records x 4 uint32: each path of a bucket of width D is
+ *               D + 1 records, the header {val, prod z, 0, 0} and the elements
+ *               {z, lo, hi, bits} sorted by feature (floats as IEEE-754 bit
+ *               patterns); bits = feature | 0x80000000 (NaN satisfies every
+ *               merged split) | 0x40000000 (categorical: lo and hi hold the low
+ *               and high 32 bits of the merged category set) | 0x20000000
+ *               (values that are no category satisfy it); padding elements are
+ *               {1, -inf, +inf, n_features | 0x80000000}
+ *   path_leaf   host, n_paths: global node index of each path's leaf
+ *   path_width  host, n_paths: the width D of each path's bucket
+ * Buckets come in increasing width, the paths of a bucket in tree order and,
+ * within a tree, left subtree first.  Other arguments as
+ * qts_load_ensemble_cat (is_categorical may be NULL).  Errors as
+ * qts_load_ensemble_cat, plus QTS_ERR_ARG when a buffer is NULL on the second
+ * call.
+ */
+qts_status qts_describe_paths(int32_t n_trees, const int64_t *tree_node_offsets, const int32_t *left,
+                              const int32_t *right, const int32_t *feature, const float *threshold,
+                              const uint8_t *default_left, const float *z, const float *leaf_value,
+                              const uint8_t *is_categorical, const uint64_t *category_left_mask,
+                              int32_t n_features, int64_t *n_records, int64_t *n_paths,
+                              uint32_t *records, int64_t *path_leaf, int32_t *path_width);
+
 /* Gauss-Legendre nodes/weights on [0,1] used by the kernels (fp64, ascending). */
 qts_status qts_gauss_legendre(int32_t n, double *t, double *w);
 

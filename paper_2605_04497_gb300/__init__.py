@@ -26,7 +26,7 @@ EXPORTS = ("qts_load_ensemble", "qts_load_ensemble_cat", "qts_update_params", "q
            "qts_shap_interactions",
            "qts_shap_interactions_noalloc", "qts_shap_interactions3", "qts_shap_interactions_order",
            "qts_shap_backward", "qts_batched_fwd_bwd", "qts_autotune", "qts_sync_status",
-           "qts_get_info", "qts_describe_ensemble", "qts_selftest_wait_timeout", "qts_batched_kernel_count", "qts_batched_last_kernel_ms", "qts_gauss_legendre", "qts_last_error",
+           "qts_get_info", "qts_describe_ensemble", "qts_describe_paths", "qts_selftest_wait_timeout", "qts_batched_kernel_count", "qts_batched_last_kernel_ms", "qts_gauss_legendre", "qts_last_error",
            "qts_free")
 
 _lib = None
@@ -85,6 +85,7 @@ def lib():
         L.qts_describe_ensemble.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, u32,
                                             ctypes.POINTER(QtsInfo)]
         L.qts_gauss_legendre.argtypes = [i32, vp, vp]
+        L.qts_describe_paths.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp]
         L.qts_batched_kernel_count.argtypes = []
         L.qts_batched_last_kernel_ms.argtypes = [ctypes.POINTER(ctypes.c_float)]
         L.qts_last_error.argtypes = []
@@ -141,6 +142,27 @@ def describe(ens, fp64: bool = False) -> dict:
     _check(lib().qts_describe_ensemble(len(a[0]) - 1, *[x.ctypes.data for x in a], int(ens.n_features),
                                        QTS_FLAG_FP64 if fp64 else 0, ctypes.byref(i)))
     return _info_dict(i)
+
+
+def describe_paths(ens) -> dict:
+    """Host-only: the FP32 path tables the library would upload (records as
+    n_records x 4 uint32 bit patterns, each path's leaf and bucket width)."""
+    arr = lambda a, dt: np.ascontiguousarray(a, dtype=dt)
+    a = [arr(ens.node_offsets, np.int64), arr(ens.left, np.int32), arr(ens.right, np.int32),
+         arr(ens.feature, np.int32), arr(ens.threshold, np.float32), arr(ens.default_left, np.uint8),
+         arr(ens.z, np.float32), arr(ens.leaf_value, np.float32)]
+    is_cat = getattr(ens, "is_cat", None)
+    cat = [arr(is_cat, np.uint8), arr(ens.cat_left, np.uint64)] if is_cat is not None else None
+    cat_ptrs = [c.ctypes.data for c in cat] if cat else [None, None]
+    n_rec, n_path = ctypes.c_int64(), ctypes.c_int64()
+    args = [len(a[0]) - 1, *[x.ctypes.data for x in a], *cat_ptrs, int(ens.n_features),
+            ctypes.byref(n_rec), ctypes.byref(n_path)]
+    _check(lib().qts_describe_paths(*args, None, None, None))
+    rec = np.zeros((n_rec.value, 4), np.uint32)
+    leaf = np.zeros(n_path.value, np.int64)
+    width = np.zeros(n_path.value, np.int32)
+    _check(lib().qts_describe_paths(*args, rec.ctypes.data, leaf.ctypes.data, width.ctypes.data))
+    return dict(records=rec, path_leaf=leaf, path_width=width)
 
 
 class Ensemble:

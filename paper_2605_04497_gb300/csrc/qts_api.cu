@@ -384,6 +384,38 @@ qts_status qts_describe_ensemble(int32_t n_trees, const int64_t* off, const int3
     return QTS_OK;
 }
 
+qts_status qts_describe_paths(int32_t n_trees, const int64_t* off, const int32_t* left, const int32_t* right,
+                              const int32_t* feature, const float* threshold, const uint8_t* default_left,
+                              const float* z, const float* leaf_value, const uint8_t* is_categorical,
+                              const uint64_t* category_left_mask, int32_t n_features, int64_t* n_records,
+                              int64_t* n_paths, uint32_t* records, int64_t* path_leaf, int32_t* path_width) {
+    if (!n_records || !n_paths || n_trees < 1 || !off || !left || !right || !feature || !threshold || !z ||
+        !leaf_value)
+        return fail(QTS_ERR_ARG, "NULL argument or n_trees < 1");
+    if (n_features < 1 || n_features > QTS_MAX_FEATURES)
+        return fail(QTS_ERR_UNSUPPORTED, "n_features out of range");
+    if (is_categorical && !category_left_mask) return fail(QTS_ERR_ARG, "category_left_mask is NULL");
+    for (int t = 0; t < n_trees; ++t)
+        if (off[t + 1] <= off[t]) return fail(QTS_ERR_ARG, "tree_node_offsets must be increasing");
+    std::vector<uint8_t> defl;
+    if (!default_left) defl.assign((size_t)off[n_trees], 1);
+    Prepared P;
+    std::string err;
+    qts_status st = prepare(n_trees, off, left, right, feature, threshold,
+                            default_left ? default_left : defl.data(), z, leaf_value, is_categorical,
+                            category_left_mask, n_features, false, &P, &err);
+    if (st != QTS_OK) return fail(st, err);
+    *n_records = (int64_t)P.rec32.size();
+    *n_paths = P.n_paths;
+    if (!records) return QTS_OK;
+    if (!path_leaf || !path_width) return fail(QTS_ERR_ARG, "path_leaf or path_width is NULL");
+    std::memcpy(records, P.rec32.data(), P.rec32.size() * sizeof(Rec32));
+    std::memcpy(path_leaf, P.path_leaf.data(), P.path_leaf.size() * sizeof(int64_t));
+    for (const Bucket& b : P.buckets)
+        for (int64_t p = 0; p < b.n_paths; ++p) path_width[b.path_base + p] = b.D;
+    return QTS_OK;
+}
+
 void qts_free(qts_ensemble* e) {
     if (!e) return;
     batch_forget(e);

@@ -132,3 +132,107 @@ def test_feature_with_both_split_types_is_rejected():
     with pytest.raises(qts.QtsError) as ei:
         qts.Ensemble.from_arrays(ens)
     assert ei.value.status == 1 and "numerical and categorical" in str(ei.value)
+
+
+# ------------------------------------------------ path tables, bit for bit
+
+def _bucket_width(d):
+    if d <= 16:
+        return d
+    for w in (20, 24, 28, 32, 40, 48, 56, 64):
+        if d <= w:
+            return w
+    raise ValueError(d)
+
+
+def _expected_tables(ens):
+    """The merged paths written out from the tree arrays (Sec. 2, Eq. q_def):
+    per leaf, the splits on each feature merged into one element with z the
+    product of the edge weights (in FP64, rounded once), [lo, hi) the
+    intersection of the numerical intervals, the intersection of the
+    categorical sets, and NaN / other-value flags; elements sorted by feature,
+    padded to the bucket width."""
+    f32 = lambda v: int(np.float32(v).view(np.uint32))
+    F = ens.n_features
+    is_cat = getattr(ens, "is_cat", None)
+    paths = []  # (width, tree order index, leaf, records)
+    order = 0
+    for t in range(ens.n_trees):
+        base = int(ens.node_offsets[t])
+        if ens.left[base] < 0:
+            continue
+        stack = [(0, [])]
+        while stack:  # left subtree first
+            v, edges = stack.pop()
+            g = base + v
+            if ens.left[g] >= 0:
+                for side, c in ((1, int(ens.right[g])), (0, int(ens.left[g]))):
+                    stack.append((c, edges + [(g, base + c, side == 0)]))
+                continue
+            elems = {}
+            for (p, c, went_left) in edges:
+                f = int(ens.feature[p])
+                e = elems.setdefault(f, dict(z=1.0, lo=-np.inf, hi=np.inf, nan=True, cat=False,
+                                             cats=(1 << 64) - 1, other=True))
+                e["z"] *= float(ens.z[c])
+                if is_cat is not None and is_cat[p]:
+                    m = int(ens.cat_left[p])
+                    e["cat"] = True
+                    e["cats"] &= m if went_left else ((1 << 64) - 1) ^ m
+                    if went_left:
+                        e["other"] = False
+                elif went_left:
+                    e["hi"] = min(e["hi"], float(ens.threshold[p]))
+                else:
+                    e["lo"] = max(e["lo"], float(ens.threshold[p]))
+                if went_left != bool(ens.default_left[p]):
+                    e["nan"] = False
+            d = len(elems)
+            D = _bucket_width(d)
+            zprod = 1.0
+            recs = []
+            for f in sorted(elems):
+                e = elems[f]
+                zprod *= e["z"]
+                bits = f | (0x80000000 if e["nan"] else 0)
+                if e["cat"]:
+                    bits |= 0x40000000 | (0x20000000 if e["other"] else 0)
+                    lo, hi = e["cats"] & 0xFFFFFFFF, e["cats"] >> 32
+                else:
+                    lo, hi = f32(e["lo"]), f32(e["hi"])
+                recs.append([f32(e["z"]), lo, hi, bits])
+            recs += [[f32(1.0), f32(-np.inf), f32(np.inf), F | 0x80000000]] * (D - d)
+            head = [f32(float(ens.leaf_value[g])), f32(zprod), 0, 0]
+            paths.append((D, order, g, [head] + recs))
+            order += 1
+    paths.sort(key=lambda p: (p[0], p[1]))
+    rec = np.array([r for p in paths for r in p[3]], dtype=np.uint64).astype(np.uint32)
+    return rec, np.array([p[2] for p in paths]), np.array([p[0] for p in paths])
+
+
+@pytest.mark.parametrize("case", ["repeated", "wide", "categorical"])
+def test_path_tables_bit_for_bit(case):
+    """The library's prepared tables equal the merged paths written out in
+    Python from the tree arrays, bit for bit (row a1 of the hot path)."""
+    from helpers import caterpillar_ensemble, categorical_ensemble
+
+    if case == "repeated":
+        ens = tiny_ensemble(3300, n_trees=5, depth=11, F=5, n_train=3000)
+        rng = np.random.default_rng(3300)
+        ens.default_left[:] = rng.integers(0, 2, ens.n_nodes).astype(np.uint8)
+    elif case == "wide":
+        ens = caterpillar_ensemble(3301, (3, 18, 33, 62), 64)
+    else:
+        ens = categorical_ensemble(3302, n_trees=4, depth=9, F=5, cat_features=(0, 3))
+    got = qts.describe_paths(ens)
+    rec, leaf, width = _expected_tables(ens)
+    assert np.array_equal(got["path_leaf"], leaf)
+    assert np.array_equal(got["path_width"], width)
+    assert got["records"].shape == rec.shape
+    assert np.array_equal(got["records"], rec)
+    if case == "categorical":
+        assert (rec[:, 3] & 0x40000000).any() and ((rec[:, 3] & 0x60000000) == 0x60000000).any()
+    if case == "wide":
+        assert set(width) >= {3, 20, 40, 64}
+    if case == "repeated":
+        assert not ((rec[:, 3] & 0x80000000) != 0).all()  # some merged elements reject NaN
