@@ -156,6 +156,11 @@ void extract_trees(int t0, int t1, const int64_t* off, const int32_t* left, cons
         int64_t base = off[t];
         int64_t nt = off[t + 1] - base;
         if (left[base] < 0) {  // single-leaf tree: no split, only the bias
+            if (nt != 1) {
+                out->st = QTS_ERR_ARG;
+                out->err = "tree " + std::to_string(t) + " has nodes that its root does not reach";
+                return;
+            }
             out->empty_leaf.push_back(base);
             out->empty_val.push_back((double)leaf[base]);
             out->n_leaves++;
@@ -258,6 +263,11 @@ void extract_trees(int t0, int t1, const int64_t* off, const int32_t* left, cons
                 stack.push_back({c, it.depth + 1, e});
             }
         }
+        if (visited != nt) {
+            out->st = QTS_ERR_ARG;
+            out->err = "tree " + std::to_string(t) + " has nodes that its root does not reach";
+            return;
+        }
     }
 }
 
@@ -301,10 +311,17 @@ static qts_status validate(int32_t n_trees, const int64_t* off, const int32_t* l
         if (b <= a) { *err = "tree " + std::to_string(t) + " has no nodes"; return QTS_ERR_ARG; }
         int64_t n = b - a;
         if (n > INT32_MAX) { *err = "tree too large"; return QTS_ERR_ARG; }
+        // a proper binary tree: every node but the root has exactly one parent,
+        // and every node is reached from the root (checked by the walk below)
+        std::vector<uint8_t> parents((size_t)n, 0);
         for (int64_t g = a; g < b; ++g) {
             int32_t l = left[g], r = right[g];
             if ((l < 0) != (r < 0) || l >= n || r >= n || (l >= 0 && (l == 0 || r == 0 || l == r))) {
                 *err = "bad children at node " + std::to_string(g);
+                return QTS_ERR_ARG;
+            }
+            if (l >= 0 && (++parents[l] > 1 || ++parents[r] > 1)) {
+                *err = "tree " + std::to_string(t) + " is not a tree (a node has two parents)";
                 return QTS_ERR_ARG;
             }
             if (l >= 0) {

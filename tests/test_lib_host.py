@@ -236,3 +236,37 @@ def test_path_tables_bit_for_bit(case):
         assert set(width) >= {3, 20, 40, 64}
     if case == "repeated":
         assert not ((rec[:, 3] & 0x80000000) != 0).all()  # some merged elements reject NaN
+
+
+def test_host_rejects_malformed_models():
+    """Bad input is refused on the host with an error code before any device
+    work: too many features, a NaN threshold, a non-finite leaf value, a node
+    reached twice, a self-loop, offsets that do not increase."""
+    spec, ens = golden_trees()[0]
+
+    def expect(bad, status, fn=qts.describe):
+        with pytest.raises(qts.QtsError) as e:
+            fn(bad)
+        assert e.value.status == status, (e.value.status, str(e.value))
+
+    big = ens.copy()
+    big.n_features = 641
+    expect(big, 4)
+    expect(big, 4, qts.describe_paths)
+    bad = ens.copy()
+    bad.threshold[0] = np.nan
+    expect(bad, 1)
+    bad = ens.copy()
+    bad.leaf_value[2] = np.inf
+    expect(bad, 1, qts.describe_paths)
+    # node 1 reached from the root and from node 1 itself
+    bad = ens.copy()
+    bad.left[1], bad.right[1] = 3, 1
+    expect(bad, 1)
+    # two parents share a child: node 3 hangs below node 0 and node 1
+    bad = ens.copy()
+    bad.right[0] = 3
+    expect(bad, 1)
+    bad = ens.copy()
+    bad.node_offsets = np.array([0, 5, 5], np.int64)
+    expect(bad, 1)
