@@ -365,6 +365,34 @@ qts_status qts_describe_paths(int32_t n_trees, const int64_t *tree_node_offsets,
                               int32_t n_features, int64_t *n_records, int64_t *n_paths,
                               uint32_t *records, int64_t *path_leaf, int32_t *path_width);
 
+/*
+ * qts_describe_alg1_program - host-only: the record program that
+ * qts_shap_values_alg1 walks (Algorithm 1, Sec. 5), for inspection and tests.
+ * No device memory is touched.  Call once with records == NULL to get
+ * *n_records, then again with buffers.
+ *   records   host, n_records x 8 uint32: one record per internal node, each
+ *             tree's nodes in preorder (a node, then its left subtree, then its
+ *             right subtree): {threshold, zc_left, zc_right, z_before, val_left,
+ *             val_right, meta, depth} (floats as IEEE-754 bit patterns).
+ *             zc_c = the product of the edge weights on the node's feature from
+ *             the root down to and including the edge into child c; z_before =
+ *             the same product above the node (1 when the feature is new on the
+ *             path); val_c = child c's leaf value, 0 for an internal child;
+ *             meta = feature | (depth of the nearest ancestor splitting on the
+ *             same feature, 127 if none) << 16 | (child 0 is a leaf) << 23 |
+ *             (child 1 is a leaf) << 24 | (NaN goes left) << 25; depth = the
+ *             node's depth (root 0)
+ *   tree_off  host, n_trees + 1: first record of each tree
+ *   levels    host, 1: deepest internal node's depth + 1
+ * Arguments otherwise as qts_load_ensemble.  Errors as qts_load_ensemble, plus
+ * QTS_ERR_UNSUPPORTED for internal nodes more than 62 levels deep.
+ */
+qts_status qts_describe_alg1_program(int32_t n_trees, const int64_t *tree_node_offsets,
+                                     const int32_t *left, const int32_t *right, const int32_t *feature,
+                                     const float *threshold, const uint8_t *default_left, const float *z,
+                                     const float *leaf_value, int32_t n_features, int64_t *n_records,
+                                     uint32_t *records, int64_t *tree_off, int32_t *levels);
+
 /* Gauss-Legendre nodes/weights on [0,1] used by the kernels (fp64, ascending). */
 qts_status qts_gauss_legendre(int32_t n, double *t, double *w);
 

@@ -26,7 +26,7 @@ EXPORTS = ("qts_load_ensemble", "qts_load_ensemble_cat", "qts_update_params", "q
            "qts_shap_interactions",
            "qts_shap_interactions_noalloc", "qts_shap_interactions3", "qts_shap_interactions_order",
            "qts_shap_backward", "qts_batched_fwd_bwd", "qts_autotune", "qts_sync_status",
-           "qts_get_info", "qts_describe_ensemble", "qts_describe_paths", "qts_selftest_wait_timeout", "qts_batched_kernel_count", "qts_batched_last_kernel_ms", "qts_gauss_legendre", "qts_last_error",
+           "qts_get_info", "qts_describe_ensemble", "qts_describe_paths", "qts_describe_alg1_program", "qts_selftest_wait_timeout", "qts_batched_kernel_count", "qts_batched_last_kernel_ms", "qts_gauss_legendre", "qts_last_error",
            "qts_free")
 
 _lib = None
@@ -85,6 +85,7 @@ def lib():
         L.qts_describe_ensemble.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, u32,
                                             ctypes.POINTER(QtsInfo)]
         L.qts_gauss_legendre.argtypes = [i32, vp, vp]
+        L.qts_describe_alg1_program.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp]
         L.qts_describe_paths.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp]
         L.qts_batched_kernel_count.argtypes = []
         L.qts_batched_last_kernel_ms.argtypes = [ctypes.POINTER(ctypes.c_float)]
@@ -163,6 +164,23 @@ def describe_paths(ens) -> dict:
     width = np.zeros(n_path.value, np.int32)
     _check(lib().qts_describe_paths(*args, rec.ctypes.data, leaf.ctypes.data, width.ctypes.data))
     return dict(records=rec, path_leaf=leaf, path_width=width)
+
+
+def describe_alg1_program(ens) -> dict:
+    """Host-only: the preorder record program of the depth-first form (records
+    as n_records x 8 uint32 bit patterns, per-tree offsets, stack levels)."""
+    arr = lambda a, dt: np.ascontiguousarray(a, dtype=dt)
+    a = [arr(ens.node_offsets, np.int64), arr(ens.left, np.int32), arr(ens.right, np.int32),
+         arr(ens.feature, np.int32), arr(ens.threshold, np.float32), arr(ens.default_left, np.uint8),
+         arr(ens.z, np.float32), arr(ens.leaf_value, np.float32)]
+    n = ctypes.c_int64()
+    args = [len(a[0]) - 1, *[x.ctypes.data for x in a], int(ens.n_features), ctypes.byref(n)]
+    _check(lib().qts_describe_alg1_program(*args, None, None, None))
+    rec = np.zeros((n.value, 8), np.uint32)
+    off = np.zeros(len(a[0]), np.int64)
+    levels = ctypes.c_int32()
+    _check(lib().qts_describe_alg1_program(*args, rec.ctypes.data, off.ctypes.data, ctypes.byref(levels)))
+    return dict(records=rec, tree_off=off, levels=levels.value)
 
 
 class Ensemble:

@@ -36,6 +36,7 @@
 // chunk of trees, accumulates phi in a private shared-memory tile in FP32 and
 // adds it to the FP64 output once per chunk.
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "qts_device.cuh"
@@ -402,8 +403,17 @@ __global__ void __launch_bounds__(kDfsMaxWarps * 32) dfs_kernel(DfsArgs a) {
 
 namespace {
 
+// The model's node arrays, as given to the loader.
+struct DfsModel {
+    const int64_t* off;
+    const int32_t *left, *right, *feature;
+    const float *thr, *z, *leaf;
+    const uint8_t* defl;
+    int32_t n_trees, n_features;
+};
+
 struct DfsBuilder {
-    const qts_ensemble* e;
+    DfsModel e;
     int64_t base;
     std::vector<DfsRec>* out;
     std::vector<double> zcur;  // merged z of each feature on the current path
@@ -418,29 +428,29 @@ struct DfsBuilder {
         }
         max_depth = std::max(max_depth, depth);
         const int64_t g = base + v;
-        const int f = e->feature[g];
-        const int32_t ch[2] = {e->left[g], e->right[g]};
+        const int f = e.feature[g];
+        const int32_t ch[2] = {e.left[g], e.right[g]};
         const bool seen = anc[f] >= 0;
         const double zold = seen ? zcur[f] : 1.0;
         DfsRec r;
-        r.thr = e->thr[g];
+        r.thr = e.thr[g];
         r.zold = (float)zold;
         bool leaf[2];
         for (int c = 0; c < 2; ++c) {
             const int64_t gc = base + ch[c];
-            leaf[c] = e->left[gc] < 0;
-            r.zc[c] = (float)(zold * (double)e->z[gc]);
-            r.val[c] = leaf[c] ? e->leaf[gc] : 0.f;
+            leaf[c] = e.left[gc] < 0;
+            r.zc[c] = (float)(zold * (double)e.z[gc]);
+            r.val[c] = leaf[c] ? e.leaf[gc] : 0.f;
         }
         r.meta = (uint32_t)f | ((uint32_t)(seen ? anc[f] : (int)kDfsNoAnc) << 16) |
-                 ((uint32_t)leaf[0] << 23) | ((uint32_t)leaf[1] << 24) | ((uint32_t)(e->defl[g] != 0) << 25);
+                 ((uint32_t)leaf[0] << 23) | ((uint32_t)leaf[1] << 24) | ((uint32_t)(e.defl[g] != 0) << 25);
         r.depth = (uint32_t)depth;
         out->push_back(r);
         for (int c = 0; c < 2; ++c) {
             if (leaf[c]) continue;
             const double zs = zcur[f];
             const int as = anc[f];
-            zcur[f] = zold * (double)e->z[base + ch[c]];
+            zcur[f] = zold * (double)e.z[base + ch[c]];
             anc[f] = depth;
             visit(ch[c], depth + 1);
             zcur[f] = zs;
@@ -450,26 +460,40 @@ struct DfsBuilder {
     }
 };
 
+// The preorder record program of every tree (host); recs and off are filled,
+// levels receives the deepest internal node's depth + 1.
+qts_status dfs_program(const DfsModel& m, std::vector<DfsRec>* recs, std::vector<int64_t>* off, int* levels) {
+    recs->clear();
+    off->assign((size_t)m.n_trees + 1, 0);
+    DfsBuilder b;
+    b.e = m;
+    b.out = recs;
+    b.zcur.assign((size_t)m.n_features, 1.0);
+    b.anc.assign((size_t)m.n_features, -1);
+    for (int t = 0; t < m.n_trees; ++t) {
+        b.base = m.off[t];
+        if (m.left[b.base] >= 0) b.visit(0, 0);
+        if (b.too_deep)
+            return fail(QTS_ERR_UNSUPPORTED, "a tree has internal nodes deeper than " +
+                                                 std::to_string(kDfsMaxLevels - 1) + " (depth-first form)");
+        (*off)[t + 1] = (int64_t)recs->size();
+    }
+    *levels = b.max_depth + 1;
+    return QTS_OK;
+}
+
 }  // namespace
 
 qts_status build_dfs_program(qts_ensemble* e) {
     if (e->d_dfs) return QTS_OK;
     if (e->left.empty()) return fail(QTS_ERR_ARG, "ensemble has no host model");
     std::vector<DfsRec> recs;
-    std::vector<int64_t> off((size_t)e->n_trees + 1, 0);
-    DfsBuilder b;
-    b.e = e;
-    b.out = &recs;
-    b.zcur.assign((size_t)e->n_features, 1.0);
-    b.anc.assign((size_t)e->n_features, -1);
-    for (int t = 0; t < e->n_trees; ++t) {
-        b.base = e->off[t];
-        if (e->left[b.base] >= 0) b.visit(0, 0);
-        if (b.too_deep)
-            return fail(QTS_ERR_UNSUPPORTED, "a tree has internal nodes deeper than " +
-                                                 std::to_string(kDfsMaxLevels - 1) + " (depth-first form)");
-        off[t + 1] = (int64_t)recs.size();
-    }
+    std::vector<int64_t> off;
+    int levels = 0;
+    const DfsModel m{e->off.data(), e->left.data(), e->right.data(), e->feature.data(), e->thr.data(),
+                     e->z.data(), e->leaf.data(), e->defl.data(), e->n_trees, e->n_features};
+    qts_status st = dfs_program(m, &recs, &off, &levels);
+    if (st != QTS_OK) return st;
     DfsRec* d_rec = nullptr;
     int64_t* d_off = nullptr;
     cudaError_t ce = cudaMalloc(&d_rec, std::max<size_t>(recs.size(), 1) * sizeof(DfsRec));
@@ -484,7 +508,7 @@ qts_status build_dfs_program(qts_ensemble* e) {
     }
     e->d_dfs = d_rec;
     e->d_dfs_off = d_off;
-    e->dfs_levels = b.max_depth + 1;
+    e->dfs_levels = levels;
     e->dfs_records = (int64_t)recs.size();
     return QTS_OK;
 }
@@ -568,5 +592,41 @@ extern "C" qts_status qts_shap_values_alg1(qts_ensemble* e, const float* X, int6
     dfs_kernel<<<(unsigned)blocks, wpb * 32, smem, s>>>(a);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return cuda_fail(ce, "depth-first kernel launch");
+    return QTS_OK;
+}
+
+extern "C" qts_status qts_describe_alg1_program(int32_t n_trees, const int64_t* off, const int32_t* left,
+                                                const int32_t* right, const int32_t* feature,
+                                                const float* threshold, const uint8_t* default_left,
+                                                const float* z, const float* leaf_value, int32_t n_features,
+                                                int64_t* n_records, uint32_t* records, int64_t* tree_off,
+                                                int32_t* levels) {
+    if (!n_records || n_trees < 1 || !off || !left || !right || !feature || !threshold || !z || !leaf_value)
+        return fail(QTS_ERR_ARG, "NULL argument or n_trees < 1");
+    if (n_features < 1 || n_features > QTS_MAX_FEATURES)
+        return fail(QTS_ERR_UNSUPPORTED, "n_features out of range");
+    for (int t = 0; t < n_trees; ++t)
+        if (off[t + 1] <= off[t]) return fail(QTS_ERR_ARG, "tree_node_offsets must be increasing");
+    // the same validation as the loader (path preparation also checks the trees)
+    std::vector<uint8_t> defl;
+    if (!default_left) defl.assign((size_t)off[n_trees], 1);
+    const uint8_t* dl = default_left ? default_left : defl.data();
+    Prepared P;
+    std::string err;
+    qts_status st = prepare(n_trees, off, left, right, feature, threshold, dl, z, leaf_value, nullptr, nullptr,
+                            n_features, false, &P, &err);
+    if (st != QTS_OK) return fail(st, err);
+    std::vector<DfsRec> recs;
+    std::vector<int64_t> toff;
+    int lv = 0;
+    const DfsModel m{off, left, right, feature, threshold, z, leaf_value, dl, n_trees, n_features};
+    st = dfs_program(m, &recs, &toff, &lv);
+    if (st != QTS_OK) return st;
+    *n_records = (int64_t)recs.size();
+    if (!records) return QTS_OK;
+    if (!tree_off || !levels) return fail(QTS_ERR_ARG, "tree_off or levels is NULL");
+    std::memcpy(records, recs.data(), recs.size() * sizeof(DfsRec));
+    std::memcpy(tree_off, toff.data(), toff.size() * sizeof(int64_t));
+    *levels = lv;
     return QTS_OK;
 }

@@ -146,9 +146,12 @@ class Ensemble:
 
 
 def concat(parts) -> Ensemble:
+    """The trees of every part, in order, as one ensemble (each part may hold
+    several trees)."""
     offs = [0]
     for p in parts:
-        offs.append(offs[-1] + p.n_nodes)
+        base = offs[-1]
+        offs.extend(int(base + o) for o in p.node_offsets[1:])
     cat = lambda name: np.concatenate([getattr(p, name) for p in parts])
     kw = {}
     if any(p.is_cat is not None for p in parts):

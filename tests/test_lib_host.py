@@ -270,3 +270,54 @@ def test_host_rejects_malformed_models():
     bad = ens.copy()
     bad.node_offsets = np.array([0, 5, 5], np.int64)
     expect(bad, 1)
+
+
+def _expected_alg1_program(ens):
+    """Algorithm 1's per-node data written out from the tree arrays: internal
+    nodes in preorder, the merged z of the node's feature before it and through
+    each child edge (FP64 products, rounded once), the nearest ancestor on the
+    same feature, leaf flags and values."""
+    f32 = lambda v: int(np.float32(v).view(np.uint32))
+    recs, off, deepest = [], [0], -1
+    for t in range(ens.n_trees):
+        base = int(ens.node_offsets[t])
+
+        def visit(v, depth, zcur, anc):
+            nonlocal deepest
+            g = base + v
+            deepest = max(deepest, depth)
+            f = int(ens.feature[g])
+            ch = (int(ens.left[g]), int(ens.right[g]))
+            zold = zcur.get(f, 1.0)
+            leaf = [ens.left[base + c] < 0 for c in ch]
+            meta = f | (anc.get(f, 127) << 16) | (int(leaf[0]) << 23) | (int(leaf[1]) << 24) | \
+                (int(ens.default_left[g] != 0) << 25)
+            recs.append([f32(ens.threshold[g]), f32(zold * float(ens.z[base + ch[0]])),
+                         f32(zold * float(ens.z[base + ch[1]])), f32(zold),
+                         f32(ens.leaf_value[base + ch[0]] if leaf[0] else 0.0),
+                         f32(ens.leaf_value[base + ch[1]] if leaf[1] else 0.0), meta, depth])
+            for i, c in enumerate(ch):
+                if not leaf[i]:
+                    visit(c, depth + 1, {**zcur, f: zold * float(ens.z[base + c])}, {**anc, f: depth})
+
+        if ens.left[base] >= 0:
+            visit(0, 0, {}, {})
+        off.append(len(recs))
+    return np.array(recs, dtype=np.uint64).astype(np.uint32), np.array(off), deepest + 1
+
+
+def test_alg1_program_bit_for_bit():
+    """The depth-first form's record program equals the per-node data written
+    out in Python from the tree arrays, bit for bit, on trees with repeated
+    features and random default directions plus a single-leaf tree."""
+    base = tiny_ensemble(3400, n_trees=4, depth=12, F=4, n_train=3000)
+    rng = np.random.default_rng(3400)
+    base.default_left[:] = rng.integers(0, 2, base.n_nodes).astype(np.uint8)
+    stump = synth.Ensemble([0, 1], [-1], [-1], [0], [0.0], [1], [1.0], [2.5], [1], 4)
+    ens = synth.concat([base, stump, base.tree(2)])
+    got = qts.describe_alg1_program(ens)
+    rec, off, levels = _expected_alg1_program(ens)
+    assert np.array_equal(got["tree_off"], off)
+    assert got["levels"] == levels
+    assert np.array_equal(got["records"], rec)
+    assert ((rec[:, 6] >> 16) & 127 != 127).any()  # repeated features occur
