@@ -479,3 +479,30 @@ def _reaches(ens, v, target):
     if ens.left[v] < 0:
         return False
     return _reaches(ens, int(ens.left[v]), target) or _reaches(ens, int(ens.right[v]), target)
+
+
+def test_categorical_gradient_matches_finite_differences():
+    """The analytic gradient with categorical splits against central
+    differences of the brute force (phi is linear in each leaf value and each
+    edge weight, so the difference is exact to rounding)."""
+    from helpers import categorical_ensemble
+
+    ens = categorical_ensemble(3500, n_trees=2, depth=5, F=3, cat_features=(0,), n_categories=5)
+    X = synth.categorical_columns(synth.normal(3500, 1, (5, 3)), (0,), 5, 3500)
+    G = synth.normal(3500, 2, (5, 4))
+    d_leaf, d_z = oracle.grad_exact(ens, X, G)
+    roots = set(int(o) for o in ens.node_offsets[:-1])
+    checked = 0
+    for n in range(ens.n_nodes):
+        for name, g in (("leaf_value", d_leaf), ("z", d_z)):
+            if (name == "leaf_value" and ens.left[n] >= 0) or (name == "z" and n in roots):
+                continue
+            h = 1.0 if name == "leaf_value" else 1e-2
+            ep, em = ens.copy(), ens.copy()
+            getattr(ep, name)[n] += np.float32(h)
+            getattr(em, name)[n] -= np.float32(h)
+            hp = float(getattr(ep, name)[n]) - float(getattr(em, name)[n])
+            fd = (_loss_brute(ep, X, G) - _loss_brute(em, X, G)) / hp
+            assert abs(fd - g[n]) <= 1e-10 * max(1.0, abs(g[n])), (name, n, fd, g[n])
+            checked += 1
+    assert checked > 20
