@@ -506,3 +506,17 @@ def test_categorical_gradient_matches_finite_differences():
             assert abs(fd - g[n]) <= 1e-10 * max(1.0, abs(g[n])), (name, n, fd, g[n])
             checked += 1
     assert checked > 20
+
+
+@pytest.mark.parametrize("s", [3, 4])
+def test_any_order_categorical_exact_equals_brute_force(s):
+    from helpers import categorical_ensemble
+
+    ens = categorical_ensemble(3600 + s, n_trees=2, depth=8, F=6, cat_features=(1, 4))
+    X = synth.categorical_columns(synth.normal(3600 + s, 1, (4, 6)), (1, 4), 6, 3600 + s)
+    ex = oracle.sii_order_exact(ens, X, s)
+    for r in range(X.shape[0]):
+        bf = oracle.brute_force_order(ens, X[r], s)
+        assert np.abs(ex[r] - bf).max() < 1e-12 * max(1.0, np.abs(bf).max()), (s, r)
+        a1 = oracle.alg1_order(ens, X[r], s, 8)
+        assert np.abs(a1 - bf).max() < 1e-12 * max(1.0, np.abs(bf).max()), (s, r)
