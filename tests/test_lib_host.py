@@ -206,8 +206,8 @@ def _expected_tables(ens):
             paths.append((D, order, g, [head] + recs))
             order += 1
     paths.sort(key=lambda p: (p[0], p[1]))
-    rec = np.array([r for p in paths for r in p[3]], dtype=np.uint64).astype(np.uint32)
-    return rec, np.array([p[2] for p in paths]), np.array([p[0] for p in paths])
+    rec = np.array([r for p in paths for r in p[3]], dtype=np.uint64).reshape(-1, 4).astype(np.uint32)
+    return rec, np.array([p[2] for p in paths], dtype=np.int64), np.array([p[0] for p in paths], dtype=np.int32)
 
 
 @pytest.mark.parametrize("case", ["repeated", "wide", "categorical"])

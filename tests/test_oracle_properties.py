@@ -37,3 +37,24 @@ def test_exact_expansion_against_brute_force(seed, F, depth, n_trees, categorica
         for f in range(F):
             if f not in used:
                 assert phi[r, f] == 0.0 and not sii[r, f].any()
+
+
+@settings(max_examples=40, deadline=None, derandomize=True, database=None)
+@given(seed=st.integers(0, 10**6), F=st.integers(1, 9), depth=st.integers(0, 14), n_trees=st.integers(1, 4),
+       categorical=st.booleans())
+def test_library_path_tables_bit_for_bit(seed, F, depth, n_trees, categorical):
+    """The library's host path preparation (no device) against the merged
+    paths written out in Python from the tree arrays, on random trees."""
+    import paper_2605_04497_gb300 as qts
+    from test_lib_host import _expected_tables
+
+    ens = synth.grow(seed, n_trees, depth, F, 800, 1.0, min_rows=2)
+    rng = np.random.default_rng(seed)
+    ens.default_left[:] = rng.integers(0, 2, ens.n_nodes).astype(np.uint8)
+    if categorical:
+        ens = synth.make_categorical(ens, (F - 1,), 4, seed + 3)
+    got = qts.describe_paths(ens)
+    rec, leaf, width = _expected_tables(ens)
+    assert np.array_equal(got["path_leaf"], leaf)
+    assert np.array_equal(got["path_width"], width)
+    assert np.array_equal(got["records"], rec)
