@@ -58,3 +58,22 @@ def test_library_path_tables_bit_for_bit(seed, F, depth, n_trees, categorical):
     assert np.array_equal(got["path_leaf"], leaf)
     assert np.array_equal(got["path_width"], width)
     assert np.array_equal(got["records"], rec)
+
+
+@settings(max_examples=40, deadline=None, derandomize=True, database=None)
+@given(seed=st.integers(0, 10**6), F=st.integers(1, 9), depth=st.integers(0, 14), n_trees=st.integers(1, 4))
+def test_library_alg1_program_bit_for_bit(seed, F, depth, n_trees):
+    """The depth-first form's record program against the per-node data written
+    out in Python from the tree arrays, on random trees."""
+    import paper_2605_04497_gb300 as qts
+    from test_lib_host import _expected_alg1_program
+
+    ens = synth.grow(seed, n_trees, depth, F, 800, 1.0, min_rows=2)
+    rng = np.random.default_rng(seed)
+    ens.default_left[:] = rng.integers(0, 2, ens.n_nodes).astype(np.uint8)
+    got = qts.describe_alg1_program(ens)
+    rec, off, levels = _expected_alg1_program(ens)
+    assert np.array_equal(got["tree_off"], off)
+    assert np.array_equal(got["records"], rec.reshape(-1, 8))
+    if len(rec):
+        assert got["levels"] == levels
