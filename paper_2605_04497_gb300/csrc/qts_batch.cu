@@ -7,6 +7,8 @@
 // item k from the atomic counter finds its segment by binary search.  For a
 // request with grad_phi one pass over each (sample, path) yields both phi and
 // the adjoint sums (the forward products P_j S_j are part of the adjoint's).
+//
+// qts-build-parts: 9 (part 0: host code; parts 1-8: one register class each)
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -32,9 +34,6 @@ struct SegDev {
     int32_t pad;
 };
 
-// Requests with F + 1 <= kPrivRows use per-warp private phi tiles (plain
-// read-add-write); wider ones share one tile with shared-memory atomics.
-constexpr int kPrivRows = 64;
 // Widths that run the fused pass with sample-pair packing when the 64-sample
 // tile fits the class's shared memory.  The register classes below are cut so
 // that every packed width fits its class's cap without spilling.
@@ -78,7 +77,7 @@ inline int64_t tile_floats_for(int priv, int F) {
                      : (priv == 1 ? (int64_t)kBatchWarps * (F + 1) * kTileLd : (int64_t)(F + 1) * kTileLd);
 }
 
-size_t batch_smem_bytes(int64_t tile_floats, int sub, int dmax) {
+inline size_t batch_smem_bytes(int64_t tile_floats, int sub, int dmax) {
     size_t off = (size_t)tile_floats * 4;
     off = (off + 15) & ~(size_t)15;
     off += 2 * (size_t)sub * (dmax + 1) * sizeof(Rec32);
@@ -95,30 +94,10 @@ struct BatchNP {
     static constexpr int fwd = D <= 8 ? 8 : 2;
 };
 
-// out[c * Mpad + s] = in[s * ld + c] for c < ncols, s < M; zero elsewhere
-// (rows up to nrows, columns up to Mpad).
-__global__ void transpose_pad_kernel(const float* __restrict__ in, int64_t M, int ncols, int64_t ld,
-                                     float* __restrict__ out, int nrows, int64_t Mpad, int* has_nan) {
-    __shared__ float tile[32][33];
-    const int64_t s0 = (int64_t)blockIdx.x * 32;
-    const int c0 = blockIdx.y * 32;
-    int nan_seen = 0;
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int64_t s = s0 + r;
-        const int c = c0 + threadIdx.x;
-        float v = 0.f;
-        if (s < M && c < ncols) v = in[s * ld + c];
-        nan_seen |= (v != v);
-        tile[r][threadIdx.x] = v;
-    }
-    __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int c = c0 + r;
-        const int64_t s = s0 + threadIdx.x;
-        if (c < nrows && s < Mpad) out[(int64_t)c * Mpad + s] = tile[threadIdx.x][r];
-    }
-    if (has_nan && nan_seen) atomicOr(has_nan, 1);
-}
+template <int C>
+cudaError_t launch_batch_class(const BatchArgs& a, size_t smem, cudaStream_t st, int* blocks_out);
+
+#if QTS_DEVICE_PARTS
 
 template <int D>
 __device__ __forceinline__ bool batch_item(const SegDev& sg, const ReqDev& rq, int64_t p0, int64_t p1,
@@ -228,7 +207,8 @@ __device__ __forceinline__ bool batch_item(const SegDev& sg, const ReqDev& rq, i
 
 // Register classes: DCLASS 8 handles widths 1..6 (4 blocks of 128 threads per
 // SM, 128 registers), 12 handles 7..10 (3 blocks, 168 registers), 16 handles
-// 11..16 (2 blocks, 255 registers), 32 handles 20..32 and 64 handles 40..64.
+// 11..16 (2 blocks, 255 registers), 32 handles 20..32, and each of the widths
+// 40, 48, 56 and 64 (which spill) is a class of its own.
 // With two samples per lane a width needs about as many registers as twice
 // that width with one, so the cuts sit lower than the widths' names suggest.
 template <int DCLASS>
@@ -294,13 +274,88 @@ __global__ void __launch_bounds__(128, DCLASS == 8 ? 4 : (DCLASS == 12 ? 3 : (DC
             }
         } else {
             switch (sg.D) {
-                QTS_CASE(40) QTS_CASE(48) QTS_CASE(56) QTS_CASE(64)
+                QTS_CASE(DCLASS)
                 default: break;
             }
         }
 #undef QTS_CASE
         if (!ok) break;  // a bounded wait ran out: status is set, stop this block
     }
+}
+
+template <int C>
+cudaError_t launch_batch_class(const BatchArgs& a, size_t smem, cudaStream_t st, int* blocks_out) {
+    auto k = batch_kernel<C>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, smem);
+    if (e != cudaSuccess) return e;
+    const int blocks = std::max(1, per_sm) * num_sms();
+    *blocks_out = blocks;
+    k<<<blocks, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+#define QTS_INST(C) \
+    template cudaError_t launch_batch_class<C>(const BatchArgs&, size_t, cudaStream_t, int*);
+#if QTS_IN_PART(1)
+QTS_INST(8)
+#endif
+#if QTS_IN_PART(2)
+QTS_INST(12)
+#endif
+#if QTS_IN_PART(3)
+QTS_INST(16)
+#endif
+#if QTS_IN_PART(4)
+QTS_INST(32)
+#endif
+#if QTS_IN_PART(5)
+QTS_INST(40)
+#endif
+#if QTS_IN_PART(6)
+QTS_INST(48)
+#endif
+#if QTS_IN_PART(7)
+QTS_INST(56)
+#endif
+#if QTS_IN_PART(8)
+QTS_INST(64)
+#endif
+#undef QTS_INST
+
+#endif  // QTS_DEVICE_PARTS
+
+#if !QTS_HOST_PART
+}  // namespace qts
+#endif
+
+#if QTS_HOST_PART
+
+// out[c * Mpad + s] = in[s * ld + c] for c < ncols, s < M; zero elsewhere
+// (rows up to nrows, columns up to Mpad).
+__global__ void transpose_pad_kernel(const float* __restrict__ in, int64_t M, int ncols, int64_t ld,
+                                     float* __restrict__ out, int nrows, int64_t Mpad, int* has_nan) {
+    __shared__ float tile[32][33];
+    const int64_t s0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    int nan_seen = 0;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t s = s0 + r;
+        const int c = c0 + threadIdx.x;
+        float v = 0.f;
+        if (s < M && c < ncols) v = in[s * ld + c];
+        nan_seen |= (v != v);
+        tile[r][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int c = c0 + r;
+        const int64_t s = s0 + threadIdx.x;
+        if (c < nrows && s < Mpad) out[(int64_t)c * Mpad + s] = tile[threadIdx.x][r];
+    }
+    if (has_nan && nan_seen) atomicOr(has_nan, 1);
 }
 
 // ------------------------------------------------------------- host side --
@@ -346,27 +401,17 @@ void batch_forget(const qts_ensemble* e) {
     }
 }
 
-int batch_class(int D) { return D <= 6 ? 8 : D <= 10 ? 12 : (D <= 16 ? 16 : (D <= 32 ? 32 : 64)); }
-static int class_index(int cls) { return cls == 8 ? 0 : cls == 12 ? 1 : cls == 16 ? 2 : cls == 32 ? 3 : 4; }
+// widths 40, 48, 56 and 64 (bucket widths) are classes of their own
+int batch_class(int D) { return D <= 6 ? 8 : D <= 10 ? 12 : (D <= 16 ? 16 : (D <= 32 ? 32 : D)); }
+constexpr int kClasses = 8;
+static int class_index(int cls) {
+    return cls == 8 ? 0 : cls == 12 ? 1 : cls == 16 ? 2 : cls == 32 ? 3 : cls == 40 ? 4 : cls == 48 ? 5 : cls == 56 ? 6 : 7;
+}
 // shared memory one block of a class may use and still reach its blocks per SM
 static size_t class_smem_budget(int cls) {
     const size_t sm = 227 * 1024;
     const int blocks = cls == 8 ? 4 : cls == 12 ? 3 : cls == 16 ? 2 : 1;
     return sm / blocks - 1024;
-}
-
-template <int C>
-static cudaError_t launch_batch_class(const BatchArgs& a, size_t smem, cudaStream_t st, int* blocks_out) {
-    auto k = batch_kernel<C>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, smem);
-    if (e != cudaSuccess) return e;
-    const int blocks = std::max(1, per_sm) * num_sms();
-    *blocks_out = blocks;
-    k<<<blocks, 128, smem, st>>>(a);
-    return cudaGetLastError();
 }
 
 // paths per work item: about 2^23 FP32 operations per item
@@ -409,6 +454,10 @@ static cudaError_t launch_transpose(const float* in, int64_t M, int ncols, int64
     return cudaGetLastError();
 }
 
+// Requests with F + 1 <= kPrivRows use per-warp private phi tiles (plain
+// read-add-write); wider ones share one tile with shared-memory atomics.
+constexpr int kPrivRows = 64;
+
 static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, BatchPlan* plan,
                              cudaStream_t cap) {
     struct SegHost {
@@ -418,7 +467,7 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
     };
     std::vector<SegHost> segs;
     std::vector<ReqDev> rd(n);
-    int64_t tile_need[5] = {0, 0, 0, 0, 0};  // per register class index
+    int64_t tile_need[kClasses] = {0, 0, 0, 0, 0, 0, 0, 0};  // per register class index
     const int sub = 32;                        // paths per staged sub-chunk
     for (int r = 0; r < n; ++r) {
         const qts_request& R = reqs[r];
@@ -542,6 +591,9 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
         else if (cls == 12) err = launch_batch_class<12>(a, smem, cap, &blocks);
         else if (cls == 16) err = launch_batch_class<16>(a, smem, cap, &blocks);
         else if (cls == 32) err = launch_batch_class<32>(a, smem, cap, &blocks);
+        else if (cls == 40) err = launch_batch_class<40>(a, smem, cap, &blocks);
+        else if (cls == 48) err = launch_batch_class<48>(a, smem, cap, &blocks);
+        else if (cls == 56) err = launch_batch_class<56>(a, smem, cap, &blocks);
         else err = launch_batch_class<64>(a, smem, cap, &blocks);
         ++kernels;
     }
@@ -670,3 +722,5 @@ extern "C" qts_status qts_batched_last_kernel_ms(float* ms) {
     if (ce == cudaSuccess) ce = cudaEventElapsedTime(ms, g_last_plan->ev0, g_last_plan->ev1);
     return ce == cudaSuccess ? QTS_OK : cuda_fail(ce, "batched kernel timing");
 }
+
+#endif  // QTS_HOST_PART

@@ -15,6 +15,8 @@
 // per-path sums over a tile of 32 samples are reduced in the warp and added to
 // FP64 per-path / per-element accumulators, which an epilogue chains to the
 // tree's edges:  dL/dw_e = dL/dz_k * prod_{other edges e' merged into k} w_e'.
+//
+// qts-build-parts: 6 (part 0: host code; parts 1-5: the per-width kernels)
 #include <algorithm>
 #include <type_traits>
 
@@ -41,6 +43,12 @@ struct BwdArgs {
     QuadD qd;
 };
 
+template <int D>
+cudaError_t launch_bwd_d(const BwdArgs& a, int np, bool fp64, bool with_phi, int warps, int64_t blocks,
+                         size_t smem, cudaStream_t st);
+
+#if QTS_DEVICE_PARTS
+
 // --------------------------------------------------------------- kernel ---
 
 template <typename Rec, typename Acc>
@@ -63,17 +71,6 @@ __device__ __forceinline__ void bwd_smem_layout(int F, int sub, int D, bool with
     off += (size_t)sub * (D + 1) * sizeof(Rec);
     off = (off + 15) & ~(size_t)15;
     *bars = (uint64_t*)(base + off);
-}
-
-size_t bwd_smem_bytes(int F, int sub, int D, bool fp64, bool with_phi) {
-    const size_t rows = F + 1;
-    size_t off = 2 * rows * kTileLd * 4;
-    off = (off + 15) & ~(size_t)15;
-    if (with_phi) off += rows * kTileLd * (fp64 ? 8 : 4);
-    off = (off + 15) & ~(size_t)15;
-    off += 2 * (size_t)sub * (D + 1) * (fp64 ? sizeof(Rec64) : sizeof(Rec32));
-    off = (off + 15) & ~(size_t)15;
-    return off + 16;
 }
 
 template <int D, int NP, bool FP64, bool WITH_PHI>
@@ -139,6 +136,71 @@ __global__ void __launch_bounds__(256) bwd_kernel(BwdArgs a) {
     }
 }
 
+// ---------------------------------------------------------- launchers -----
+
+template <int D, int NP, bool FP64, bool WP>
+static cudaError_t launch_bwd_t(const BwdArgs& a, int warps, int64_t blocks, size_t smem, cudaStream_t st) {
+    auto k = bwd_kernel<D, NP, FP64, WP>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<(unsigned)blocks, warps * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_bwd_d(const BwdArgs& a, int np, bool fp64, bool with_phi, int warps,
+                                int64_t blocks, size_t smem, cudaStream_t st) {
+    if (fp64) return launch_bwd_t<D, 2, true, false>(a, warps, blocks, smem, st);
+    if constexpr (D <= 8) {
+        if (np >= 4) {
+            if (with_phi) return launch_bwd_t<D, 4, false, true>(a, warps, blocks, smem, st);
+            return launch_bwd_t<D, 4, false, false>(a, warps, blocks, smem, st);
+        }
+    }
+    if (with_phi) return launch_bwd_t<D, 2, false, true>(a, warps, blocks, smem, st);
+    return launch_bwd_t<D, 2, false, false>(a, warps, blocks, smem, st);
+}
+
+#define QTS_INST(DD) \
+    template cudaError_t launch_bwd_d<DD>(const BwdArgs&, int, bool, bool, int, int64_t, size_t, cudaStream_t);
+#if QTS_IN_PART(1)
+QTS_INST(64)
+#endif
+#if QTS_IN_PART(2)
+QTS_INST(56)
+#endif
+#if QTS_IN_PART(3)
+QTS_INST(48) QTS_INST(40)
+#endif
+#if QTS_IN_PART(4)
+QTS_INST(32) QTS_INST(28) QTS_INST(24) QTS_INST(20)
+#endif
+#if QTS_IN_PART(5)
+QTS_INST(1) QTS_INST(2) QTS_INST(3) QTS_INST(4) QTS_INST(5) QTS_INST(6) QTS_INST(7) QTS_INST(8) QTS_INST(9) QTS_INST(10) QTS_INST(11) QTS_INST(12) QTS_INST(13) QTS_INST(14) QTS_INST(15) QTS_INST(16)
+#endif
+#undef QTS_INST
+
+#endif  // QTS_DEVICE_PARTS
+
+#if !QTS_HOST_PART
+}  // namespace qts
+#endif
+
+#if QTS_HOST_PART
+
+size_t bwd_smem_bytes(int F, int sub, int D, bool fp64, bool with_phi) {
+    const size_t rows = F + 1;
+    size_t off = 2 * rows * kTileLd * 4;
+    off = (off + 15) & ~(size_t)15;
+    if (with_phi) off += rows * kTileLd * (fp64 ? 8 : 4);
+    off = (off + 15) & ~(size_t)15;
+    off += 2 * (size_t)sub * (D + 1) * (fp64 ? sizeof(Rec64) : sizeof(Rec32));
+    off = (off + 15) & ~(size_t)15;
+    return off + 16;
+}
+
 // ------------------------------------------------------------ epilogue ----
 
 // G = sum_s grad_phi[s, F]  (the weight of E[f] in L), FP64.
@@ -195,33 +257,6 @@ __global__ void slot_epilogue_kernel(SlotMap sm, const double* __restrict__ g_sl
         const double tot = g_slot[s] + G * path_val[p] * zexcl[s];
         for (int64_t e = e0; e < e1; ++e) atomicAdd(&d_z[enode[e]], tot * ecoef[e]);
     }
-}
-
-// ---------------------------------------------------------- launchers -----
-
-template <int D, int NP, bool FP64, bool WP>
-static cudaError_t launch_bwd_t(const BwdArgs& a, int warps, int64_t blocks, size_t smem, cudaStream_t st) {
-    auto k = bwd_kernel<D, NP, FP64, WP>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    k<<<(unsigned)blocks, warps * 32, smem, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <int D>
-static cudaError_t launch_bwd_d(const BwdArgs& a, int np, bool fp64, bool with_phi, int warps,
-                                int64_t blocks, size_t smem, cudaStream_t st) {
-    if (fp64) return launch_bwd_t<D, 2, true, false>(a, warps, blocks, smem, st);
-    if constexpr (D <= 8) {
-        if (np >= 4) {
-            if (with_phi) return launch_bwd_t<D, 4, false, true>(a, warps, blocks, smem, st);
-            return launch_bwd_t<D, 4, false, false>(a, warps, blocks, smem, st);
-        }
-    }
-    if (with_phi) return launch_bwd_t<D, 2, false, true>(a, warps, blocks, smem, st);
-    return launch_bwd_t<D, 2, false, false>(a, warps, blocks, smem, st);
 }
 
 cudaError_t launch_bwd_bucket(const qts_ensemble* e, const Bucket& b, const float* X,
@@ -336,3 +371,5 @@ extern "C" qts_status qts_shap_backward(qts_ensemble* e, const float* X, int64_t
     if (ce != cudaSuccess) return cuda_fail(ce, "adjoint epilogue");
     return QTS_OK;
 }
+
+#endif  // QTS_HOST_PART

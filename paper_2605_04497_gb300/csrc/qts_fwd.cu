@@ -10,6 +10,8 @@
 // adds (o_i - z_i) c_i to phi[s, f_i] in a shared FP32 tile.  Path records are
 // staged in shared memory by bulk (TMA) copies, double-buffered; the FP32 tile
 // is flushed into the FP64 output with atomics once per block.
+//
+// qts-build-parts: 6 (part 0: host code; parts 1-5: the per-width kernels)
 #include <algorithm>
 #include <type_traits>
 
@@ -35,6 +37,12 @@ struct FwdArgs {
     QuadF q;
     QuadD qd;
 };
+
+template <int D>
+cudaError_t launch_fwd_d(const FwdArgs& a, int np, bool fp64, int warps, int64_t blocks, size_t smem,
+                         cudaStream_t st);
+
+#if QTS_DEVICE_PARTS
 
 // --------------------------------------------------------------- kernel ---
 
@@ -135,22 +143,6 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
     }
 }
 
-// phi[:, :F] = 0, phi[:, F] = E[f]
-__global__ void phi_init_kernel(double* phi, int64_t M, int F, double bias) {
-    const int64_t n = M * (F + 1);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        phi[i] = (i % (F + 1) == F) ? bias : 0.0;
-}
-
-cudaError_t launch_phi_init(double* phi, int64_t M, int F, double bias, cudaStream_t st) {
-    if (M <= 0) return cudaSuccess;
-    const int64_t n = M * (F + 1);
-    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4 * 152);
-    phi_init_kernel<<<blocks, 256, 0, st>>>(phi, M, F, bias);
-    return cudaGetLastError();
-}
-
 // ---------------------------------------------------------- dispatch ------
 
 template <int D, int NP, bool FP64>
@@ -166,8 +158,8 @@ static cudaError_t launch_fwd_t(const FwdArgs& a, int warps, int64_t blocks, siz
 }
 
 template <int D>
-static cudaError_t launch_fwd_d(const FwdArgs& a, int np, bool fp64, int warps, int64_t blocks,
-                                size_t smem, cudaStream_t st) {
+cudaError_t launch_fwd_d(const FwdArgs& a, int np, bool fp64, int warps, int64_t blocks, size_t smem,
+                         cudaStream_t st) {
     if (fp64) return launch_fwd_t<D, 2, true>(a, warps, blocks, smem, st);
     if constexpr (D <= 8) {
         if (np >= 8) return launch_fwd_t<D, 8, false>(a, warps, blocks, smem, st);
@@ -176,6 +168,50 @@ static cudaError_t launch_fwd_d(const FwdArgs& a, int np, bool fp64, int warps, 
         if (np >= 4) return launch_fwd_t<D, 4, false>(a, warps, blocks, smem, st);
     }
     return launch_fwd_t<D, 2, false>(a, warps, blocks, smem, st);
+}
+
+#define QTS_INST(DD) \
+    template cudaError_t launch_fwd_d<DD>(const FwdArgs&, int, bool, int, int64_t, size_t, cudaStream_t);
+#if QTS_IN_PART(1)
+QTS_INST(64)
+#endif
+#if QTS_IN_PART(2)
+QTS_INST(56)
+#endif
+#if QTS_IN_PART(3)
+QTS_INST(48) QTS_INST(40)
+#endif
+#if QTS_IN_PART(4)
+QTS_INST(32) QTS_INST(28) QTS_INST(24) QTS_INST(20)
+#endif
+#if QTS_IN_PART(5)
+QTS_INST(1) QTS_INST(2) QTS_INST(3) QTS_INST(4) QTS_INST(5) QTS_INST(6) QTS_INST(7) QTS_INST(8)
+QTS_INST(9) QTS_INST(10) QTS_INST(11) QTS_INST(12) QTS_INST(13) QTS_INST(14) QTS_INST(15) QTS_INST(16)
+#endif
+#undef QTS_INST
+
+#endif  // QTS_DEVICE_PARTS
+
+#if !QTS_HOST_PART
+}  // namespace qts
+#endif
+
+#if QTS_HOST_PART
+
+// phi[:, :F] = 0, phi[:, F] = E[f]
+__global__ void phi_init_kernel(double* phi, int64_t M, int F, double bias) {
+    const int64_t n = M * (F + 1);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        phi[i] = (i % (F + 1) == F) ? bias : 0.0;
+}
+
+cudaError_t launch_phi_init(double* phi, int64_t M, int F, double bias, cudaStream_t st) {
+    if (M <= 0) return cudaSuccess;
+    const int64_t n = M * (F + 1);
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4 * 152);
+    phi_init_kernel<<<blocks, 256, 0, st>>>(phi, M, F, bias);
+    return cudaGetLastError();
 }
 
 size_t fwd_smem_bytes(int F, int sub, int D, bool fp64, int ntiles) {
@@ -229,4 +265,7 @@ cudaError_t launch_fwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
     }
 }
 
+
 }  // namespace qts
+
+#endif  // QTS_HOST_PART

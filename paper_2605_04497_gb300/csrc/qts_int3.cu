@@ -8,6 +8,8 @@
 // Triples are stored compactly (a < b < c, see tri3_index) and accumulated in
 // FP64 in the workspace laid out [triple][sample] (one coalesced 256-byte add
 // per warp and triple); a finalize kernel writes [sample][triple] in FP32.
+//
+// qts-build-parts: 5 (part 0: host code; parts 1-4: the per-width kernels)
 #include <algorithm>
 #include <string>
 
@@ -38,6 +40,11 @@ struct Int3Args {
     int* status;
     QuadF q;
 };
+
+template <int D>
+cudaError_t launch_int3_d(const Int3Args& a, int64_t blocks, size_t smem, cudaStream_t st);
+
+#if QTS_DEVICE_PARTS
 
 template <int D, int NP, bool HAS_NAN>
 __device__ __forceinline__ void int3_path_f32(const Rec32* __restrict__ r, const float* __restrict__ xs,
@@ -118,14 +125,6 @@ __device__ __forceinline__ void int3_path_f32(const Rec32* __restrict__ r, const
     }
 }
 
-size_t int3_smem_bytes(int F, int sub, int D) {
-    size_t off = (size_t)(F + 1) * kTileLd * 4;
-    off = (off + 15) & ~(size_t)15;
-    off += 2 * (size_t)sub * (D + 1) * sizeof(Rec32);
-    off = (off + 15) & ~(size_t)15;
-    return off + 16;
-}
-
 template <int D, int NP>
 __global__ void __launch_bounds__(256) int3_kernel(Int3Args a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -149,13 +148,58 @@ __global__ void __launch_bounds__(256) int3_kernel(Int3Args a) {
         mbar_fence_init();
         s_phase[0] = s_phase[1] = 0;
     }
-    const bool has_nan = load_tile_t(xs, a.X, s0, a.M, F, F, 1) || a.cat != 0;
+    // The edge test is per element and the work per triple, so the NaN- and
+    // category-aware test costs nothing measurable here: one variant serves all.
+    (void)load_tile_t(xs, a.X, s0, a.M, F, F, 1);
     const int64_t s = s0 + lane;
     (void)stream_paths<Rec32, D>(a.rec, p0, p1, a.sub, st0, st1, bars, s_phase, &s_flag, a.status,
                                  [&](int64_t, const Rec32* r) {
-                                     if (has_nan) int3_path_f32<D, NP, true>(r, xs, a.acc, s, a.M, lane, F, a.q);
-                                     else int3_path_f32<D, NP, false>(r, xs, a.acc, s, a.M, lane, F, a.q);
+                                     int3_path_f32<D, NP, true>(r, xs, a.acc, s, a.M, lane, F, a.q);
                                  });
+}
+
+template <int D>
+cudaError_t launch_int3_d(const Int3Args& a, int64_t blocks, size_t smem, cudaStream_t st) {
+    constexpr int NP = D <= 6 ? 8 : (D <= 12 ? 4 : 2);
+    auto k = int3_kernel<D, NP>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<(unsigned)blocks, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+
+#define QTS_INST(DD) template cudaError_t launch_int3_d<DD>(const Int3Args&, int64_t, size_t, cudaStream_t);
+#if QTS_IN_PART(1)
+QTS_INST(16)
+#endif
+#if QTS_IN_PART(2)
+QTS_INST(15)
+#endif
+#if QTS_IN_PART(3)
+QTS_INST(14) QTS_INST(3) QTS_INST(4) QTS_INST(5) QTS_INST(6) QTS_INST(7) QTS_INST(8)
+#endif
+#if QTS_IN_PART(4)
+QTS_INST(13) QTS_INST(9) QTS_INST(10) QTS_INST(11) QTS_INST(12)
+#endif
+#undef QTS_INST
+
+#endif  // QTS_DEVICE_PARTS
+
+#if !QTS_HOST_PART
+}  // namespace qts
+#endif
+
+#if QTS_HOST_PART
+
+size_t int3_smem_bytes(int F, int sub, int D) {
+    size_t off = (size_t)(F + 1) * kTileLd * 4;
+    off = (off + 15) & ~(size_t)15;
+    off += 2 * (size_t)sub * (D + 1) * sizeof(Rec32);
+    off = (off + 15) & ~(size_t)15;
+    return off + 16;
 }
 
 // out[s][t] = acc[t][s] (FP64 -> FP32), one thread per (triple, sample).
@@ -166,18 +210,6 @@ __global__ void int3_finalize_kernel(const double* __restrict__ acc, int64_t M, 
         const int64_t t = i / M, s = i - t * M;
         out[s * n_tri + t] = (float)acc[i];
     }
-}
-
-template <int D>
-static cudaError_t launch_int3_d(const Int3Args& a, int64_t blocks, size_t smem, cudaStream_t st) {
-    constexpr int NP = D <= 6 ? 8 : (D <= 12 ? 4 : 2);
-    auto k = int3_kernel<D, NP>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    k<<<(unsigned)blocks, 128, smem, st>>>(a);
-    return cudaGetLastError();
 }
 
 static cudaError_t launch_int3_bucket(const qts_ensemble* e, const Bucket& b, const float* X, int64_t M, int F,
@@ -248,3 +280,5 @@ extern "C" qts_status qts_shap_interactions3(qts_ensemble* e, const float* X, in
     if (ce != cudaSuccess) return cuda_fail(ce, "third-order finalize launch");
     return QTS_OK;
 }
+
+#endif  // QTS_HOST_PART

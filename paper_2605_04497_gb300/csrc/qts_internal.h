@@ -9,6 +9,21 @@
 
 #include "qtreeshap.h"
 
+// Heavy translation units are compiled in parts, in parallel: a file whose
+// first lines say "qts-build-parts: N" is compiled N times with -DQTS_PART=k.
+// Part 0 holds the host code and sees only declarations of the per-width
+// launchers; part k >= 1 defines the kernels and instantiates its share of the
+// launchers.  Compiled without QTS_PART, a file is one complete unit.
+#ifdef QTS_PART
+#define QTS_HOST_PART (QTS_PART == 0)
+#define QTS_DEVICE_PARTS (QTS_PART != 0)
+#define QTS_IN_PART(k) (QTS_PART == (k))
+#else
+#define QTS_HOST_PART 1
+#define QTS_DEVICE_PARTS 1
+#define QTS_IN_PART(k) 1
+#endif
+
 namespace qts {
 
 // ---------------------------------------------------------------- records --

@@ -12,6 +12,8 @@
 // in registers.  Subsets are stored compactly in lexicographic order of their
 // sorted features and accumulated in FP64 in the workspace, laid out
 // [subset][sample]; a finalize kernel writes [sample][subset] in FP32.
+//
+// qts-build-parts: 5 (part 0: host code; parts 1-4: the per-width kernels)
 #include <algorithm>
 #include <string>
 
@@ -21,7 +23,6 @@ namespace qts {
 
 constexpr int kIntkWarps = 4;
 constexpr int kIntkMaxD = 16;
-constexpr int kIntkMaxOrder = 8;
 constexpr int kIntkPairs = 4;  // node pairs per pass: all 8 nodes, one atomic per subset
 
 // C(n, R) for a compile-time R; 0 when n < R.
@@ -31,13 +32,6 @@ __host__ __device__ __forceinline__ int64_t binom_r(int64_t n) {
     int64_t v = 1;
 #pragma unroll
     for (int i = 1; i <= R; ++i) v = v * (n - R + i) / i;
-    return v;
-}
-
-static int64_t binom_host(int64_t n, int k) {
-    if (k < 0 || n < k) return 0;
-    int64_t v = 1;
-    for (int i = 1; i <= k; ++i) v = v * (n - k + i) / i;
     return v;
 }
 
@@ -71,6 +65,32 @@ struct IntkPath {
     int64_t s, M;
     double* acc;
 };
+
+// Shared-memory layout of a block, every part 16-byte aligned: per-warp S
+// (float2) and d (float) slices, per-warp features, the x tile, the two path
+// staging buffers and the barriers.
+struct IntkSmem {
+    size_t S, dd, fe, xs, st, bars, total;
+};
+
+__host__ __device__ __forceinline__ size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+__host__ __device__ __forceinline__ IntkSmem intk_smem(int F, int sub, int D) {
+    IntkSmem L;
+    L.S = 0;
+    L.dd = align16(L.S + (size_t)kIntkWarps * kIntkMaxD * kIntkPairs * 32 * sizeof(float2));
+    L.fe = align16(L.dd + (size_t)kIntkWarps * kIntkMaxD * 32 * sizeof(float));
+    L.xs = align16(L.fe + (size_t)kIntkWarps * kIntkMaxD * sizeof(int));
+    L.st = align16(L.xs + (size_t)(F + 1) * kTileLd * sizeof(float));
+    L.bars = align16(L.st + 2 * (size_t)sub * (D + 1) * sizeof(Rec32));
+    L.total = L.bars + 2 * sizeof(uint64_t);
+    return L;
+}
+
+template <int D>
+cudaError_t launch_intk_d(const IntkArgs& a, int64_t blocks, size_t smem, cudaStream_t st);
+
+#if QTS_DEVICE_PARTS
 
 // Choose the next element at position >= start with REM more to follow.  R is
 // the product of the unchosen elements before `start` (times w val), dp the
@@ -154,27 +174,6 @@ __device__ __forceinline__ void intk_path(const Rec32* __restrict__ r, const flo
     __syncwarp();  // dd, S and fe are rewritten by the warp's next path
 }
 
-// Shared-memory layout of a block, every part 16-byte aligned: per-warp S
-// (float2) and d (float) slices, per-warp features, the x tile, the two path
-// staging buffers and the barriers.
-struct IntkSmem {
-    size_t S, dd, fe, xs, st, bars, total;
-};
-
-__host__ __device__ __forceinline__ size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
-
-__host__ __device__ __forceinline__ IntkSmem intk_smem(int F, int sub, int D) {
-    IntkSmem L;
-    L.S = 0;
-    L.dd = align16(L.S + (size_t)kIntkWarps * kIntkMaxD * kIntkPairs * 32 * sizeof(float2));
-    L.fe = align16(L.dd + (size_t)kIntkWarps * kIntkMaxD * 32 * sizeof(float));
-    L.xs = align16(L.fe + (size_t)kIntkWarps * kIntkMaxD * sizeof(int));
-    L.st = align16(L.xs + (size_t)(F + 1) * kTileLd * sizeof(float));
-    L.bars = align16(L.st + 2 * (size_t)sub * (D + 1) * sizeof(Rec32));
-    L.total = L.bars + 2 * sizeof(uint64_t);
-    return L;
-}
-
 template <int D>
 __global__ void __launch_bounds__(kIntkWarps * 32) intk_kernel(IntkArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -213,6 +212,50 @@ __global__ void __launch_bounds__(kIntkWarps * 32) intk_kernel(IntkArgs a) {
                                  });
 }
 
+template <int D>
+cudaError_t launch_intk_d(const IntkArgs& a, int64_t blocks, size_t smem, cudaStream_t st) {
+    auto k = intk_kernel<D>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<(unsigned)blocks, kIntkWarps * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+#define QTS_INST(DD) \
+    template cudaError_t launch_intk_d<DD>(const IntkArgs&, int64_t, size_t, cudaStream_t);
+#if QTS_IN_PART(1)
+QTS_INST(2) QTS_INST(3) QTS_INST(4) QTS_INST(5)
+#endif
+#if QTS_IN_PART(2)
+QTS_INST(6) QTS_INST(7) QTS_INST(8) QTS_INST(9)
+#endif
+#if QTS_IN_PART(3)
+QTS_INST(10) QTS_INST(11) QTS_INST(12) QTS_INST(13)
+#endif
+#if QTS_IN_PART(4)
+QTS_INST(14) QTS_INST(15) QTS_INST(16)
+#endif
+#undef QTS_INST
+
+#endif  // QTS_DEVICE_PARTS
+
+#if !QTS_HOST_PART
+}  // namespace qts
+#endif
+
+#if QTS_HOST_PART
+
+constexpr int kIntkMaxOrder = 8;
+
+static int64_t binom_host(int64_t n, int k) {
+    if (k < 0 || n < k) return 0;
+    int64_t v = 1;
+    for (int i = 1; i <= k; ++i) v = v * (n - k + i) / i;
+    return v;
+}
+
 // out[s][t] = acc[t][s] (FP64 -> FP32), one thread per (subset, sample).
 __global__ void intk_finalize_kernel(const double* __restrict__ acc, int64_t M, int64_t n_sub,
                                      float* __restrict__ out) {
@@ -221,17 +264,6 @@ __global__ void intk_finalize_kernel(const double* __restrict__ acc, int64_t M, 
         const int64_t t = i / M, s = i - t * M;
         out[s * n_sub + t] = (float)acc[i];
     }
-}
-
-template <int D>
-static cudaError_t launch_intk_d(const IntkArgs& a, int64_t blocks, size_t smem, cudaStream_t st) {
-    auto k = intk_kernel<D>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    k<<<(unsigned)blocks, kIntkWarps * 32, smem, st>>>(a);
-    return cudaGetLastError();
 }
 
 static cudaError_t launch_intk_bucket(const qts_ensemble* e, const Bucket& b, const float* X, int64_t M, int F,
@@ -305,3 +337,5 @@ extern "C" qts_status qts_shap_interactions_order(qts_ensemble* e, const float* 
     if (ce != cudaSuccess) return cuda_fail(ce, "order-s interaction finalize launch");
     return QTS_OK;
 }
+
+#endif  // QTS_HOST_PART
