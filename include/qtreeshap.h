@@ -226,14 +226,18 @@ qts_status qts_shap_interactions_order(qts_ensemble *ens, const float *X, int64_
  * being captured into a graph that forbids allocation nodes, services with a
  * fixed memory budget whose allocator owns all device memory, or latency-bound
  * callers that cannot afford cudaMalloc's implicit device synchronisation.
- * The FP64 accumulators live in a fixed array compiled into the library
+ * The FP64 accumulators live in ONE fixed array compiled into the library
  * (16 MiB on every device that loads it, held until the process exits), so the
  * call supports (F(F-1)/2 + F) * M <= 2,097,152 and returns QTS_ERR_UNSUPPORTED,
- * with a message, beyond that.  The first call on a device looks the array's
- * address up (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Every call clears and reuses the same array, so calls that overlap
- * on the GPU (different streams, or different threads) race and give wrong
- * results: serialise them.  Arguments and output layout as qts_shap_interactions.
+ * with a message, beyond that.  The first call on a device (and the first after
+ * a reset of that device) looks the array's address up with
+ * cudaGetSymbolAddress; make that first call before any stream capture.  Every
+ * call clears the part of the array it uses and reuses it, and there is one
+ * array per device for the whole process - shared by every ensemble and every
+ * handle - so calls that overlap on the GPU (different streams, threads or
+ * ensembles) race and give wrong results: serialise all calls on a device
+ * across the process, not per ensemble.  Arguments and output layout as
+ * qts_shap_interactions.
  */
 qts_status qts_shap_interactions_noalloc(qts_ensemble *ens, const float *X, int64_t M, int32_t F,
                                          int32_t n_quad, float *phi_ij, qts_stream_t stream);

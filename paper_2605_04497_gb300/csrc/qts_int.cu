@@ -12,9 +12,16 @@
 // and first-order sums are accumulated in shared FP32 tiles and flushed into
 // FP64 accumulators in the workspace laid out [pair][sample] and
 // [feature][sample]; a finalize kernel writes the (F+1) x (F+1) matrices.
+//
+// qts-build-parts: 6 (part 0: host code; parts 1-5: the per-width kernels)
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <mutex>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "qts_device.cuh"
 
@@ -41,6 +48,12 @@ struct IntArgs {
     int* status;
     QuadF q;
 };
+
+template <int D>
+cudaError_t launch_int_d(const IntArgs& a, bool pair_smem, int warps, int64_t blocks, size_t smem,
+                         cudaStream_t st);
+
+#if QTS_DEVICE_PARTS
 
 // PAIR_SMEM: pair sums go to a shared tile [n_pairs][33]; otherwise straight to
 // the FP64 accumulator (lanes = consecutive samples, so each add is coalesced).
@@ -128,16 +141,6 @@ __device__ __forceinline__ void int_path_f32(const Rec32* __restrict__ r, const 
         if (j < nreal) atomicAdd(&ps[feat_of(r[1 + j].bits) * kTileLd + lane], dd[j] * c1[j]);
 }
 
-size_t int_smem_bytes(int F, int sub, int D, bool pair_smem) {
-    const size_t rows = F + 1;
-    size_t off = 2 * rows * kTileLd * 4;
-    if (pair_smem) off += (size_t)F * (F - 1) / 2 * kTileLd * 4;
-    off = (off + 15) & ~(size_t)15;
-    off += 2 * (size_t)sub * (D + 1) * sizeof(Rec32);
-    off = (off + 15) & ~(size_t)15;
-    return off + 16;
-}
-
 template <int D, int NP, bool PAIR_SMEM>
 __global__ void __launch_bounds__(256) int_kernel(IntArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -198,6 +201,62 @@ __global__ void __launch_bounds__(256) int_kernel(IntArgs a) {
     }
 }
 
+template <int D, int NP, bool PS>
+static cudaError_t launch_int_t(const IntArgs& a, int warps, int64_t blocks, size_t smem, cudaStream_t st) {
+    auto k = int_kernel<D, NP, PS>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<(unsigned)blocks, warps * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_int_d(const IntArgs& a, bool pair_smem, int warps, int64_t blocks, size_t smem,
+                                cudaStream_t st) {
+    constexpr int NP = D <= 6 ? 8 : (D <= 12 ? 4 : 2);
+    if (pair_smem) return launch_int_t<D, NP, true>(a, warps, blocks, smem, st);
+    return launch_int_t<D, NP, false>(a, warps, blocks, smem, st);
+}
+
+#define QTS_INST(DD) \
+    template cudaError_t launch_int_d<DD>(const IntArgs&, bool, int, int64_t, size_t, cudaStream_t);
+#if QTS_IN_PART(1)
+QTS_INST(32)
+#endif
+#if QTS_IN_PART(2)
+QTS_INST(28)
+#endif
+#if QTS_IN_PART(3)
+QTS_INST(24) QTS_INST(1) QTS_INST(2) QTS_INST(3) QTS_INST(4) QTS_INST(5) QTS_INST(6) QTS_INST(7) QTS_INST(8)
+#endif
+#if QTS_IN_PART(4)
+QTS_INST(20) QTS_INST(9) QTS_INST(10) QTS_INST(11) QTS_INST(12)
+#endif
+#if QTS_IN_PART(5)
+QTS_INST(13) QTS_INST(14) QTS_INST(15) QTS_INST(16)
+#endif
+#undef QTS_INST
+
+#endif  // QTS_DEVICE_PARTS
+
+#if !QTS_HOST_PART
+}  // namespace qts
+#endif
+
+#if QTS_HOST_PART
+
+size_t int_smem_bytes(int F, int sub, int D, bool pair_smem) {
+    const size_t rows = F + 1;
+    size_t off = 2 * rows * kTileLd * 4;
+    if (pair_smem) off += (size_t)F * (F - 1) / 2 * kTileLd * 4;
+    off = (off + 15) & ~(size_t)15;
+    off += 2 * (size_t)sub * (D + 1) * sizeof(Rec32);
+    off = (off + 15) & ~(size_t)15;
+    return off + 16;
+}
+
 // out[s][i][j] (F+1 x F+1, fp32) from the FP64 accumulators; one thread per (s, i).
 __global__ void int_finalize_kernel(const double* __restrict__ acc_pair, const double* __restrict__ acc_phi,
                                     int64_t M, int F, double bias, float* __restrict__ out) {
@@ -223,25 +282,6 @@ __global__ void int_finalize_kernel(const double* __restrict__ acc_pair, const d
         row[i] = (float)(acc_phi[(int64_t)i * M + s] - rowsum);
         row[F] = 0.f;
     }
-}
-
-template <int D, int NP, bool PS>
-static cudaError_t launch_int_t(const IntArgs& a, int warps, int64_t blocks, size_t smem, cudaStream_t st) {
-    auto k = int_kernel<D, NP, PS>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    k<<<(unsigned)blocks, warps * 32, smem, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <int D>
-static cudaError_t launch_int_d(const IntArgs& a, bool pair_smem, int warps, int64_t blocks, size_t smem,
-                                cudaStream_t st) {
-    constexpr int NP = D <= 6 ? 8 : (D <= 12 ? 4 : 2);
-    if (pair_smem) return launch_int_t<D, NP, true>(a, warps, blocks, smem, st);
-    return launch_int_t<D, NP, false>(a, warps, blocks, smem, st);
 }
 
 static constexpr size_t kSmemBudget = 200 * 1024;
@@ -328,9 +368,14 @@ extern "C" qts_status qts_shap_interactions(qts_ensemble* e, const float* X, int
 //
 // Same kernels as qts_shap_interactions, but the FP64 accumulators live in a
 // fixed device array that is part of the library image, so the call never
-// allocates.  Its address is looked up once per device with
-// cudaGetSymbolAddress (host code cannot use the array's name as a device
-// pointer).
+// allocates.  Host code cannot use the array's name as a device pointer: its
+// address comes from cudaGetSymbolAddress, with the device current.  That
+// address belongs to a context - a device reset destroys the primary context,
+// the next call creates a new one, reloads the library's module, and the array
+// may then sit elsewhere - so the looked-up address is cached under the current
+// context's process-unique id (cuCtxGetId), not under the device ordinal.  The
+// two driver calls are fetched through the runtime, so the library still links
+// no driver library of its own.
 
 namespace qts {
 
@@ -338,22 +383,59 @@ constexpr int64_t kNoAllocDoubles = (int64_t)2 * 1024 * 1024;  // 16 MiB per dev
 
 static __device__ __align__(256) double g_int_noalloc_scratch[kNoAllocDoubles];
 
+struct CtxFns {
+    PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    PFN_cuCtxGetId_v12000 get_id = nullptr;
+};
+
+static CtxFns ctx_fns() {
+    static CtxFns f;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            f.get_current = (PFN_cuCtxGetCurrent_v4000)p;
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            f.get_id = (PFN_cuCtxGetId_v12000)p;
+        cudaGetLastError();  // a missing entry point is not an error of the caller's next call
+    });
+    return f;
+}
+
+// Unique id of the context current on this thread; false when there is none
+// (the runtime has not made one current yet) or the driver cannot say.
+static bool current_ctx_id(unsigned long long* id) {
+    const CtxFns f = ctx_fns();
+    if (!f.get_current || !f.get_id) return false;
+    CUcontext ctx = nullptr;
+    if (f.get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return f.get_id(ctx, id) == CUDA_SUCCESS;
+}
+
 static std::mutex g_noalloc_mu;
-static void* g_noalloc_ptr[64] = {nullptr};
+static std::vector<std::pair<unsigned long long, void*>> g_noalloc_ptr;  // (context id, address)
 
 static qts_status noalloc_scratch(void** out) {
-    int dev = 0;
-    cudaError_t ce = cudaGetDevice(&dev);
-    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
-    if (dev < 0 || dev >= 64) return fail(QTS_ERR_UNSUPPORTED, "device ordinal above 63");
+    unsigned long long id = 0;
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        ce = cudaGetSymbolAddress(&p, g_int_noalloc_scratch);
-        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetSymbolAddress of the interaction scratch");
-        g_noalloc_ptr[dev] = p;
+    if (current_ctx_id(&id)) {
+        for (const auto& kv : g_noalloc_ptr)
+            if (kv.first == id) {
+                *out = kv.second;
+                return QTS_OK;
+            }
     }
-    *out = g_noalloc_ptr[dev];
+    void* p = nullptr;
+    cudaError_t ce = cudaGetSymbolAddress(&p, g_int_noalloc_scratch);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetSymbolAddress of the interaction scratch");
+    // the lookup makes the device's context current if none was: ask again;
+    // without an id the address is not cached and is looked up on every call
+    if (current_ctx_id(&id)) g_noalloc_ptr.emplace_back(id, p);
+    *out = p;
     return QTS_OK;
 }
 
@@ -395,3 +477,5 @@ extern "C" qts_status qts_shap_interactions_noalloc(qts_ensemble* e, const float
     if (ce != cudaSuccess) return cuda_fail(ce, "interaction finalize launch");
     return QTS_OK;
 }
+
+#endif  // QTS_HOST_PART
