@@ -1,6 +1,6 @@
 """Run one kernel case a few times, for profilers (ncu) and quick timing.
 
-    python -m paper_2605_04497_gb300.profile_case <case> [--reps R]
+    python profile_case.py <case> [--reps R]
 
 Cases (synthetic inputs from `synth`):
   forward-xgb        qts_shap_values on the 1,000-tree depth-8 ensemble, M = 10,000
@@ -32,7 +32,7 @@ import sys
 
 import numpy as np
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
