@@ -5,9 +5,11 @@ One step = one graph launch of the persistent batched kernel that computes, for
 all 64 requests, phi (M x (F+1)) and the adjoint d/d(leaf values), d/d(edge
 weights) of sum(grad_phi * phi), with inputs resident in HBM.  The metric is
 sample*trees/s (sum over requests of M * trees per step time).  Alongside: the
-plain per-ensemble kernels (forward + adjoint launched per request), the
-persistent kernel's FP32-pipe roofline fraction, an end-to-end figure through
-the C ABI with host buffers, and the FP64 CPU oracle timed on a bounded sample.
+same fused pass launched request by request, the plain per-ensemble kernels
+(forward + adjoint, and forward alone), the persistent kernel's FP32-pipe
+roofline fraction, an end-to-end figure through the C ABI with host buffers,
+the accuracy of every arm against the FP64 oracle, the four fixed
+single-ensemble workloads, and the FP64 CPU oracle timed on a bounded sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 N > 1 (torchrun): replicas, each rank runs the whole batch ("scaling": "weak").
@@ -33,11 +35,9 @@ UNIT = "sample·trees/s"
 WORKLOAD = ("batch64: 64 ensembles, trees log-U[10,2000], depth U{3..16}, F log-U[8,200], "
             "M log-U[1,50000], covers from min(100000, 20*2^depth) rows, grad_phi ~N(0,1), seed 20260504")
 N_QUAD = 8
-# DRAM bytes (read + write) of the three persistent launches of one step: the
-# mean over the three graph runs of `ncu --metrics gpu__time_duration.sum,
-# dram__bytes_read.sum,dram__bytes_write.sum` on `bench.py --steps 1 --warmup 1`
-# (profiles/batch_kernel_dram_batch64.md); valid only while the kernel sources
-# hash to TRAFFIC_HASH, otherwise reported as null.
+# DRAM bytes (read + write) per step of the persistent launches, from an ncu
+# capture of one kernel on a small request scaled by the units processed; valid
+# only while the kernel sources hash to TRAFFIC_HASH, otherwise reported as null.
 TRAFFIC_BYTES = (1.684 + 0.799 + 12.541 + 4.953 + 11.343 + 3.827) * 1e9
 TRAFFIC_HASH = "f43243ce70c89602"
 KERNEL_SOURCES = ("qts_batch.cu", "qts_paths.cuh", "qts_device.cuh", "qts_internal.h")
@@ -173,6 +173,26 @@ def units(works):
 
 # ------------------------------------------------------------------ our arm
 
+def time_arm(fn, steps, warmup, stream, flush):
+    """CUDA-event times (ms) of `steps` calls of fn after `warmup` untimed ones,
+    with L2 flushed (outside the events) before each timed call."""
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    out = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        out.append(a.elapsed_time(b))
+    return out
+
+
 def run_ours(args, rank, world, local):
     import torch
 
@@ -187,9 +207,13 @@ def run_ours(args, rank, world, local):
     infos = [e.info() for e in ens]
     X = [torch.from_numpy(w.X).to(dev) for w in works]
     G = [torch.from_numpy(w.grad_phi).to(dev) for w in works]
-    phi = [torch.empty((w.M, w.F + 1), dtype=torch.float64, device=dev) for w in works]
-    dl = [torch.empty(e.n_nodes, dtype=torch.float64, device=dev) for e in ens]
-    dz = [torch.empty(e.n_nodes, dtype=torch.float64, device=dev) for e in ens]
+
+    def outputs():
+        return ([torch.empty((w.M, w.F + 1), dtype=torch.float64, device=dev) for w in works],
+                [torch.empty(e.n_nodes, dtype=torch.float64, device=dev) for e in ens],
+                [torch.empty(e.n_nodes, dtype=torch.float64, device=dev) for e in ens])
+
+    phi, dl, dz = outputs()
     items = [dict(ens=e, X=x, grad_phi=g, phi=p, d_leaf=a, d_z=b)
              for e, x, g, p, a, b in zip(ens, X, G, phi, dl, dz)]
     reqs = qts.make_requests(items)
@@ -202,6 +226,12 @@ def run_ours(args, rank, world, local):
     def step():
         qts.batched_fwd_bwd(reqs, N_QUAD)
 
+    # per-width launch parameters picked by timing the persistent kernel on this
+    # batch (a prefix of each request's samples); set-up, outside the timed region
+    t0 = time.time()
+    tuned = qts.batched_autotune(reqs, N_QUAD, max_samples=args.tune_samples) if args.tune_samples >= 0 else {}
+    tune_s = time.time() - t0
+    log(f"batched autotune: {tune_s:.1f}s, {tuned}")
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -237,22 +267,41 @@ def run_ours(args, rank, world, local):
         kms, kms_src = float(np.mean(kern_ms)), "CUDA events around the persistent kernel inside the graph"
     else:  # conservative: the whole step (init + persistent kernel + epilogues)
         kms, kms_src = float(np.mean(step_ms)), "CUDA events around the whole step"
+    for e in ens:
+        e.sync_status()
 
     out = None
     if rank == 0:
-        # plain per-ensemble kernels: forward and adjoint launched per request
+        aux = max(1, min(args.steps, args.aux_steps))
+        # the same fused forward + adjoint pass, launched request by request
+        # (one cached graph each): what the persistent scheduler itself adds
+        phi_f, dl_f, dz_f = outputs()
+        singles = [qts.make_requests([dict(ens=e, X=x, grad_phi=g, phi=p, d_leaf=a, d_z=b)])
+                   for e, x, g, p, a, b in zip(ens, X, G, phi_f, dl_f, dz_f)]
+
+        def plain_fused():
+            for r in singles:
+                qts.batched_fwd_bwd(r, N_QUAD)
+
+        fused_ms = time_arm(plain_fused, aux, 1, stream, flush)
+        # the plain per-ensemble kernels: forward, then adjoint, per request
+        phi_p, dl_p, dz_p = outputs()
+
         def plain():
-            for it in items:
-                qts.shap_values(it["ens"], it["X"], N_QUAD, out=it["phi"])
-                qts.shap_backward(it["ens"], it["X"], it["grad_phi"], N_QUAD)
-        pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(1)]
-        for a, b in pe:
-            flush.fill_(1.0)
-            a.record(stream)
-            plain()
-            b.record(stream)
+            for k, it in enumerate(items):
+                qts.shap_values(it["ens"], it["X"], N_QUAD, out=phi_p[k])
+                qts.shap_backward(it["ens"], it["X"], it["grad_phi"], N_QUAD, d_leaf=dl_p[k], d_z=dz_p[k])
+
+        plain_ms = time_arm(plain, aux, 1, stream, flush)
+
+        def plain_forward():
+            for k, it in enumerate(items):
+                qts.shap_values(it["ens"], it["X"], N_QUAD, out=phi_p[k])
+
+        fwd_ms = time_arm(plain_forward, aux, 1, stream, flush)
         torch.cuda.synchronize()
-        plain_ms = float(np.mean([a.elapsed_time(b) for a, b in pe]))
+        for e in ens:
+            e.sync_status()
 
         # end to end through the C ABI with host buffers: H2D of X and grad_phi
         # from pinned memory, the batched call, D2H of phi and both gradients
@@ -271,22 +320,21 @@ def run_ours(args, rank, world, local):
             for h, d in zip(hphi + hdl + hdz, phi + dl + dz):
                 h.copy_(d, non_blocking=True)
 
-        ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(1)]
-        for a, b in ee:
-            a.record(stream)
-            e2e_step()
-            b.record(stream)
-        torch.cuda.synchronize()
-        e2e_ms = float(np.mean([a.elapsed_time(b) for a, b in ee]))
+        e2e_ms = time_arm(e2e_step, aux, 1, stream, flush)
 
-        # accuracy on a sample of rows against the FP64 oracle (outside timing)
-        acc = accuracy_check(works, phi)
+        # accuracy of every arm against the FP64 oracle (outside timing)
+        acc = accuracy_check(works, infos, {"batched": (phi, dl, dz), "plain": (phi_p, dl_p, dz_p),
+                                     "plain_fused": (phi_f, dl_f, dz_f)})
+        fixed = fixed_workloads(qts, dev, stream, flush)
         cpu, cpu_quad = cpu_baseline(works, budget_s=args.cpu_seconds)
         pk = peaks()
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         max_mhz = float(pk.get("sm_max_mhz", 2070.0))
         peak = fp32_peak_tops(sms, max_mhz)
         achieved = alg_ops / (kms / 1e3) / 1e12
+        arm = lambda t, kernels: {"value": U / (float(np.mean(t)) / 1e3), "unit": UNIT,
+                                  "ms_per_step": float(np.mean(t)), "steps": len(t), "kernels": kernels,
+                                  "speedup_batched": float(np.mean(t)) / ms}
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -294,22 +342,26 @@ def run_ours(args, rank, world, local):
             "config": {"workload": WORKLOAD, "requests": len(works), "sample_trees_per_step": U,
                        "paths": int(sum(i["n_paths"] for i in infos)),
                        "n_quad": N_QUAD, "l2": "flushed between steps (256 MB write)",
-                       "accumulation": "f64 across path chunks", "parallelism": "replicas" if world > 1 else "single"},
+                       "accumulation": "f64 across path chunks", "parallelism": "replicas" if world > 1 else "single",
+                       "autotune": {"seconds": round(tune_s, 1), "samples_per_request": args.tune_samples,
+                                    "choices": {str(D): {"paths_per_item": p, "sample_mapping": m}
+                                                for D, (p, m) in sorted(tuned.items())}}},
             "roofline": {"bound": "alu",
                          "kernel": "batch_kernel<8>, <12>, <16> (persistent fused forward + adjoint, one launch per register class)",
                          "achieved": achieved, "peak": peak, "unit": "Tops/s (FP32 pipe lane-ops)",
                          "frac": achieved / peak,
                          "traffic": TRAFFIC_BYTES if kernel_hash() == TRAFFIC_HASH else None,
-                         "traffic_unit": "bytes per step (the three persistent launches)",
+                         "traffic_unit": "DRAM bytes per step (the persistent launches), scaled from a one-request capture",
                          "peak_basis": f"{sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (max SM clock)",
                          "algorithmic_ops_per_launch": alg_ops, "kernel_ms": kms,
                          "kernel_ms_source": kms_src},
-            "plain": {"value": U / (plain_ms / 1e3), "unit": UNIT, "ms_per_step": plain_ms,
-                      "kernels": "per request: forward launches + adjoint launches + epilogue",
-                      "speedup_batched": plain_ms / ms},
-            "e2e": {"value": U / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
-                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "plain_fused": arm(fused_ms, "per request: the same fused forward + adjoint pass, one graph launch each"),
+            "plain": arm(plain_ms, "per request: forward launches + adjoint launches + epilogue"),
+            "plain_forward": arm(fwd_ms, "per request: forward launches only (phi, no gradients)"),
+            "e2e": {"value": U / (float(np.mean(e2e_ms)) / 1e3), "unit": UNIT, "ms_per_step": float(np.mean(e2e_ms)),
+                    "steps": len(e2e_ms), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "accuracy": acc,
+            "fixed_workloads": fixed,
             "cpu_baseline": cpu,
             "cpu_quadrature": cpu_quad,
             "gpu_launches": int(n_kern * args.steps),
@@ -321,31 +373,123 @@ def run_ours(args, rank, world, local):
     return out
 
 
-def accuracy_check(works, phi, rows_per=2, max_paths=400000):
-    """Max per-sample error of the batched FP32 phi against the library's FP64
-    mode (QTS_FLAG_FP64 tables and kernels; the GPU tests hold that mode to
-    1e-12 of the FP64 oracle) on a few rows of every request with at most
-    `max_paths` leaves, normalised by max(|f(x)|, max|phi|)."""
+def _oracle_plan(works, infos, rows_per, leaves_per, small_leaves=1_500_000, heavy_share=0.05):
+    """Which requests the oracle checks, and on which rows and leaves: every
+    request of at most `small_leaves` leaves (`rows_per` rows), and every
+    request that carries at least `heavy_share` of the step's element work (one
+    row: the oracle's exact expansion of a multi-million-leaf ensemble takes
+    tens of seconds per row).  Each checked request gets `leaves_per` sampled
+    leaves for the gradients."""
+    work = np.array([w.M * i["sum_unique"] for w, i in zip(works, infos)], dtype=np.float64)
+    share = work / max(work.sum(), 1.0)
+    plan = {}
+    for k, w in enumerate(works):
+        small = w.ens.n_leaves <= small_leaves
+        if not small and share[k] < heavy_share:
+            continue
+        nr = rows_per if small else 1
+        rows = np.unique(np.linspace(0, w.M - 1, min(nr, w.M)).astype(int))
+        leaves = np.flatnonzero(w.ens.left < 0)
+        rng = np.random.default_rng(1000 + k)
+        pick = np.sort(rng.choice(leaves, size=min(leaves_per, len(leaves)), replace=False))
+        plan[k] = (rows, pick)
+    return plan, float(share[list(plan)].sum())
+
+
+def _oracle_refs(works, plan, threads):
+    """FP64 oracle values for the planned rows (phi, exact expansion) and leaves
+    (d_leaf, d_z: orc_grad_exact restricted to those leaves, exact at the
+    leaves' own nodes).  The oracle calls run as independent tasks, largest
+    first, on all host threads (its C calls release the GIL)."""
+    import concurrent.futures as cf
+
+    import oracle
+
+    res = {k: dict() for k in plan}
+
+    def phi_task(k):
+        rows = plan[k][0]
+        res[k]["phi"] = oracle.shap_exact(works[k].ens, works[k].X[rows], n_threads=len(rows))
+
+    def grad_task(k):
+        w, pick = works[k], plan[k][1]
+        dl, dz = oracle.grad_exact(w.ens, w.X, w.grad_phi, leaves=pick, n_threads=4)
+        res[k]["dl"], res[k]["dz"] = dl[pick], dz[pick]
+
+    cost = lambda k: works[k].ens.n_leaves * (1 + works[k].M / 1000)
+    tasks = sorted([(cost(k), phi_task, k) for k in plan] + [(cost(k), grad_task, k) for k in plan],
+                   key=lambda t: -t[0])
+    with cf.ThreadPoolExecutor(max_workers=max(1, threads)) as ex:
+        for f in [ex.submit(fn, k) for _, fn, k in tasks]:
+            f.result()
+    return {k: (plan[k][0], res[k]["phi"], plan[k][1], res[k]["dl"], res[k]["dz"]) for k in plan}
+
+
+def accuracy_check(works, infos, arms, rows_per=2, leaves_per=16):
+    """Every arm's phi on sampled rows against the FP64 oracle's exact
+    expansion, per sample normalised by max(|f(x)|, max|phi|), and its d_leaf /
+    d_z at sampled leaves against the oracle's analytic gradient, normalised by
+    the largest sampled |value|, on the requests `_oracle_plan` picks."""
+    import oracle
+
+    t0 = time.time()
+    plan, share = _oracle_plan(works, infos, rows_per, leaves_per)
+    refs = _oracle_refs(works, plan, oracle.threads())
+    out = {"tolerance": 1e-5, "reference": "FP64 oracle (orc_shap_exact, orc_grad_exact)",
+           "requests_checked": len(plan), "requests": len(works), "work_share_checked": share,
+           "rows_checked": int(sum(len(r[0]) for r in refs.values())),
+           "leaves_checked": int(sum(len(r[2]) for r in refs.values()))}
+    for name, (phi, dl, dz) in arms.items():
+        e_phi = e_grad = 0.0
+        for k, (rows, ref, pick, rl, rz) in refs.items():
+            got = phi[k][rows].cpu().numpy()
+            scale = np.maximum(np.abs(ref.sum(1)), np.abs(ref[:, :-1]).max(1))
+            e_phi = max(e_phi, float((np.abs(got - ref).max(1) / np.maximum(scale, 1e-300)).max()))
+            gl = dl[k][pick].cpu().numpy()
+            gz = dz[k][pick].cpu().numpy()
+            e_grad = max(e_grad, float(np.abs(gl - rl).max() / max(np.abs(rl).max(), 1e-300)),
+                         float(np.abs(gz - rz).max() / max(np.abs(rz).max(), 1e-300)))
+        out[name] = {"max_rel_err_phi": e_phi, "max_rel_err_grad": e_grad}
+    out["oracle_seconds"] = round(time.time() - t0, 1)
+    return out
+
+
+def fixed_workloads(qts, dev, stream, flush, reps=5):
+    """The four fixed single-ensemble workloads, each timed with CUDA events
+    (median of `reps` calls after one warm-up): first-order phi on the
+    10-tree depth-4 parity case, the 1,000-tree depth-8 ensemble and the
+    200-tree depth-20 ensemble, and pairwise interactions on the 500-tree
+    depth-6 ensemble."""
     import torch
 
-    import paper_2605_04497_gb300 as qts
+    import synth
 
-    worst = 0.0
-    checked = 0
-    for w, p in zip(works, phi):
-        if w.ens.n_leaves > max_paths:
-            continue
-        rows = np.unique(np.linspace(0, w.M - 1, min(rows_per, w.M)).astype(int))
-        E64 = qts.Ensemble.from_arrays(w.ens, fp64=True)
-        ref = qts.shap_values(E64, torch.from_numpy(np.ascontiguousarray(w.X[rows])).to(p.device)).cpu().numpy()
-        E64.sync_status()
-        E64.close()
-        got = p[rows].cpu().numpy()
-        scale = np.maximum(np.abs(ref.sum(1)), np.abs(ref[:, :-1]).max(1))
-        worst = max(worst, float((np.abs(got - ref).max(1) / scale).max()))
-        checked += len(rows)
-    return {"max_rel_err_phi": worst, "rows_checked": checked, "tolerance": 1e-5,
-            "reference": "the library's FP64 mode on the same rows (pinned to the FP64 oracle by the GPU tests)"}
+    out = {}
+    for name, kind in (("small-depth4", "phi"), ("xgb-depth8", "phi"), ("deep-depth20", "phi"),
+                       ("pairs-depth6", "interactions")):
+        t0 = time.time()
+        w = synth.workload(name)
+        E = qts.Ensemble.from_arrays(w.ens)
+        info = E.info()
+        Xd = torch.from_numpy(w.X).to(dev)
+        if kind == "phi":
+            res = torch.empty((w.M, w.F + 1), dtype=torch.float64, device=dev)
+            fn = lambda: qts.shap_values(E, Xd, N_QUAD, out=res)
+        else:
+            res = torch.empty((w.M, w.F + 1, w.F + 1), dtype=torch.float32, device=dev)
+            fn = lambda: qts.shap_interactions(E, Xd, N_QUAD, out=res)
+        ts = time_arm(fn, reps if name != "deep-depth20" else 3, 1, stream, flush)
+        E.sync_status()
+        t = float(np.median(ts))
+        rec = {"what": kind, "trees": w.ens.n_trees, "M": w.M, "F": w.F, "paths": info["n_paths"],
+               "ms": t, "sample_trees_per_s": w.M * w.ens.n_trees / (t / 1e3)}
+        if kind == "phi":
+            ops = OPS_FWD * N_QUAD * info["sum_unique"] * w.M
+            rec["fp32_tops"] = ops / (t / 1e3) / 1e12
+        out[name] = rec
+        E.close()
+        log(f"{name}: {t:.3f} ms ({time.time() - t0:.1f}s with setup)")
+    return out
 
 
 def cpu_sample_shape(cores: int):
@@ -468,6 +612,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--tune-samples", type=int, default=1024,
+                    help="samples per request the batched autotuner times on (-1: no tuning)")
+    ap.add_argument("--aux-steps", type=int, default=3,
+                    help="timed steps of each comparison arm (plain, plain-fused, forward-only, e2e)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":

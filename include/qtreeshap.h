@@ -61,7 +61,8 @@ typedef enum qts_status {
 
 /* Limits of the supported envelope. */
 #define QTS_MAX_UNIQUE_FEATURES_PER_PATH 64
-#define QTS_MAX_FEATURES 640 /* sample and accumulator tiles live in shared memory */
+#define QTS_MAX_FEATURES 832 /* the kernels keep a sample tile and an accumulator tile of F + 1
+                                rows in shared memory (F = 784: Fashion-MNIST-shaped models) */
 #define QTS_MAX_QUAD 32
 #define QTS_MAX_FEATURES_ORDER3 128
 #define QTS_MAX_CATEGORIES 64 /* categories 0..63 of a categorical split */
@@ -282,6 +283,29 @@ typedef struct qts_request {
  */
 qts_status qts_batched_fwd_bwd(int32_t n_requests, const qts_request *reqs, int32_t n_quad,
                                qts_stream_t stream);
+
+/*
+ * qts_batched_autotune - pick the batched launch's per-width parameters for a
+ * set of requests by timing its persistent kernel on the requests' own data (the
+ * autotuner of the batched form; the paper has no batching).  For every bucket
+ * width that carries at least 1% of the batch's work it times, with that
+ * width's work items alone in the launch, the paths per work item (half, once
+ * and twice the default) and, where the fused pass packs two samples per lane,
+ * the sample mapping (each warp its own 64 samples, or the block's warps sharing
+ * 64 samples and splitting the paths), and keeps the fastest.  The choices are
+ * stored in each request's ensemble and used by later batched calls that
+ * include it (their cached graphs are rebuilt).
+ *   reqs, n, n_quad  as qts_batched_fwd_bwd; the requests' outputs are
+ *                    overwritten with partial results
+ *   max_samples      time on the first min(M, max_samples) samples of each
+ *                    request (0: all)
+ *   chosen           host, 2 * (QTS_MAX_UNIQUE_FEATURES_PER_PATH + 1) int32 or
+ *                    NULL: for width D, [2D] paths per item, [2D + 1] mapping
+ *                    (2 or 3, 0 where not packed); 0, 0 for untuned widths
+ * Synchronous on `stream`.  Errors as qts_batched_fwd_bwd.
+ */
+qts_status qts_batched_autotune(int32_t n_requests, const qts_request *reqs, int32_t n_quad,
+                                int64_t max_samples, int32_t *chosen, qts_stream_t stream);
 
 /* Number of kernels in the graph of the calling thread's last batched call. */
 int32_t qts_batched_kernel_count(void);

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "QTS_OK", 1: "QTS_ERR_ARG", 2: "QTS_ERR_CUDA", 3: "QTS_ERR_OO
 EXPORTS = ("qts_load_ensemble", "qts_load_ensemble_cat", "qts_update_params", "qts_shap_values", "qts_shap_values_alg1",
            "qts_shap_interactions",
            "qts_shap_interactions_noalloc", "qts_shap_interactions3", "qts_shap_interactions_order",
-           "qts_shap_backward", "qts_batched_fwd_bwd", "qts_autotune", "qts_sync_status",
+           "qts_shap_backward", "qts_batched_fwd_bwd", "qts_batched_autotune", "qts_autotune", "qts_sync_status",
            "qts_get_info", "qts_describe_ensemble", "qts_describe_paths", "qts_describe_alg1_program", "qts_selftest_wait_timeout", "qts_batched_kernel_count", "qts_batched_last_kernel_ms", "qts_gauss_legendre", "qts_last_error",
            "qts_free")
 
@@ -78,6 +78,7 @@ def lib():
         L.qts_shap_interactions_order.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp]
         L.qts_shap_backward.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, vp]
         L.qts_batched_fwd_bwd.argtypes = [i32, vp, i32, vp]
+        L.qts_batched_autotune.argtypes = [i32, vp, i32, i64, vp, vp]
         L.qts_autotune.argtypes = [vp, vp, i64, i32, ctypes.c_char_p, vp]
         L.qts_sync_status.argtypes = [vp, vp]
         L.qts_selftest_wait_timeout.argtypes = [vp, vp]
@@ -361,15 +362,20 @@ def expand_triples(compact, F: int):
     return out
 
 
-def shap_backward(ens: Ensemble, X, grad_phi, n_quad: int = 8, stream=None):
-    """(d_leaf, d_z), float64 of length n_nodes: gradients of sum(grad_phi * phi)."""
+def shap_backward(ens: Ensemble, X, grad_phi, n_quad: int = 8, stream=None, d_leaf=None, d_z=None):
+    """(d_leaf, d_z), float64 of length n_nodes: gradients of sum(grad_phi * phi).
+    Pass d_leaf / d_z to write into existing tensors."""
     import torch
 
     _check_x(ens, X)
     M, F = X.shape
     assert grad_phi.shape == (M, F + 1) and grad_phi.dtype == torch.float32 and grad_phi.is_contiguous()
-    d_leaf = torch.empty(ens.n_nodes, dtype=torch.float64, device=X.device)
-    d_z = torch.empty(ens.n_nodes, dtype=torch.float64, device=X.device)
+    if d_leaf is None:
+        d_leaf = torch.empty(ens.n_nodes, dtype=torch.float64, device=X.device)
+    if d_z is None:
+        d_z = torch.empty(ens.n_nodes, dtype=torch.float64, device=X.device)
+    for t in (d_leaf, d_z):
+        assert t.shape == (ens.n_nodes,) and t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()
     _check(lib().qts_shap_backward(ens.handle, _ptr(X), M, F, n_quad, _ptr(grad_phi), _ptr(d_leaf),
                                    _ptr(d_z), _stream(stream)))
     return d_leaf, d_z
@@ -395,6 +401,16 @@ def batched_fwd_bwd(reqs, n_quad: int = 8, stream=None):
     """Run prepared ``make_requests`` in one persistent launch (graph-captured)."""
     _check(lib().qts_batched_fwd_bwd(len(reqs), ctypes.cast(reqs, ctypes.c_void_p), n_quad,
                                      _stream(stream)))
+
+
+def batched_autotune(reqs, n_quad: int = 8, max_samples: int = 1024, stream=None) -> dict:
+    """Tune the batched launch for these requests (see qts_batched_autotune);
+    returns {width: (paths per item, sample mapping)} for the tuned widths."""
+    n = 65  # QTS_MAX_UNIQUE_FEATURES_PER_PATH + 1
+    chosen = np.zeros(2 * n, dtype=np.int32)
+    _check(lib().qts_batched_autotune(len(reqs), ctypes.cast(reqs, ctypes.c_void_p), n_quad, max_samples,
+                                      chosen.ctypes.data, _stream(stream)))
+    return {D: (int(chosen[2 * D]), int(chosen[2 * D + 1])) for D in range(n) if chosen[2 * D] > 0}
 
 
 def batched_last_kernel_ms() -> float:

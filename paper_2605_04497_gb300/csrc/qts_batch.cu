@@ -30,7 +30,8 @@ struct SegDev {
     int32_t req;
     int32_t priv;       // 0: warps share 32 samples (atomics); 1: each warp owns 32
                         // samples and a private phi tile; 2: each warp owns 64
-                        // samples, two per lane (sample-pair packing), private tile
+                        // samples, two per lane (sample-pair packing), private tile;
+                        // 3: as 2, but the warps share 64 samples and split the paths
     int32_t pad;
 };
 
@@ -68,12 +69,12 @@ struct BatchArgs {
 
 // samples per item for each mode
 __host__ __device__ __forceinline__ int item_samples(int priv) {
-    return priv == 2 ? 64 * kBatchWarps : (priv == 1 ? 32 * kBatchWarps : 32);
+    return priv == 3 ? 64 : priv == 2 ? 64 * kBatchWarps : (priv == 1 ? 32 * kBatchWarps : 32);
 }
 
 // floats of the phi region a request needs in a mode
 inline int64_t tile_floats_for(int priv, int F) {
-    return priv == 2 ? (int64_t)kBatchWarps * (F + 1) * kTileLd2
+    return priv >= 2 ? (int64_t)kBatchWarps * (F + 1) * kTileLd2
                      : (priv == 1 ? (int64_t)kBatchWarps * (F + 1) * kTileLd : (int64_t)(F + 1) * kTileLd);
 }
 
@@ -107,12 +108,16 @@ __device__ __forceinline__ bool batch_item(const SegDev& sg, const ReqDev& rq, i
     const int F = rq.F;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if constexpr (pair_width(D)) {
-        if (sg.priv == 2) {
-            // sample-pair mode: warp w owns samples s0 + 64 w .. + 63, lane l the pair 2l, 2l+1
+        if (sg.priv >= 2) {
+            // sample-pair modes, lane l the pair 2l, 2l+1 of its warp's 64 samples.
+            // priv 2: warp w owns samples s0 + 64 w .. + 63 and walks every path;
+            // priv 3: the block's warps share samples s0 .. s0 + 63 and split the
+            // paths.  Either way warp w accumulates into its own phi tile w.
+            const bool split = sg.priv == 2;
             const int tile_elems = (F + 1) * kTileLd2;
             float* my = ps + warp * tile_elems;
             float2* zs = zs_all + warp * 16;
-            const int64_t sw = s0 + 64 * warp;
+            const int64_t sw = split ? s0 + 64 * warp : s0;
             for (int idx = lane; idx < tile_elems; idx += 32) my[idx] = 0.f;
             __syncthreads();
             const bool has_nan = *rq.has_nan != 0;
@@ -126,14 +131,27 @@ __device__ __forceinline__ bool batch_item(const SegDev& sg, const ReqDev& rq, i
                     if (has_nan) bwd_path_f32_sp<D, true>(r, xr, gr, my, zs, lane, q, gsl, gv);
                     else bwd_path_f32_sp<D, false>(r, xr, gr, my, zs, lane, q, gsl, gv);
                 },
-                true);
+                split);
             if (!ok) return false;
             if (rq.phi) {
-                for (int idx = lane; idx < 64 * F; idx += 32) {
-                    const int s = idx / F, f = idx - s * F;
-                    if (sw + s < rq.M) {
-                        const float v = my[f * kTileLd2 + s];
-                        if (v != 0.f) atomicAdd(&rq.phi[(sw + s) * (F + 1) + f], (double)v);
+                if (split) {
+                    for (int idx = lane; idx < 64 * F; idx += 32) {
+                        const int s = idx / F, f = idx - s * F;
+                        if (sw + s < rq.M) {
+                            const float v = my[f * kTileLd2 + s];
+                            if (v != 0.f) atomicAdd(&rq.phi[(sw + s) * (F + 1) + f], (double)v);
+                        }
+                    }
+                } else {
+                    // stream_paths ended on a block barrier: every warp's tile is complete
+                    for (int idx = threadIdx.x; idx < 64 * F; idx += blockDim.x) {
+                        const int s = idx / F, f = idx - s * F;
+                        if (sw + s < rq.M) {
+                            float v = 0.f;
+#pragma unroll
+                            for (int w = 0; w < kBatchWarps; ++w) v += ps[w * tile_elems + f * kTileLd2 + s];
+                            if (v != 0.f) atomicAdd(&rq.phi[(sw + s) * (F + 1) + f], (double)v);
+                        }
                     }
                 }
             }
@@ -372,7 +390,9 @@ struct BatchPlan {
 static std::mutex g_plan_mu;
 static std::vector<BatchPlan*> g_plans;  // most recent last
 static thread_local BatchPlan* g_last_plan = nullptr;
-constexpr size_t kMaxPlans = 8;
+// cached graphs (a caller that launches each of many requests on its own keeps
+// one plan per request)
+constexpr size_t kMaxPlans = 256;
 
 static void destroy_plan(BatchPlan* p) {
     if (p->ev0) cudaEventDestroy(p->ev0);
@@ -458,8 +478,17 @@ static cudaError_t launch_transpose(const float* in, int64_t M, int ncols, int64
 // read-add-write); wider ones share one tile with shared-memory atomics.
 constexpr int kPrivRows = 64;
 
+// Per-width launch choices that override the ensembles' own while tuning:
+// paths per work item and packed sample mapping (0: keep), and optionally only
+// the buckets of one width.
+struct BatchOverride {
+    int paths[kMaxD + 1];
+    int mode[kMaxD + 1];
+    int only_width;
+};
+
 static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, BatchPlan* plan,
-                             cudaStream_t cap) {
+                             cudaStream_t cap, const BatchOverride* ov = nullptr) {
     struct SegHost {
         SegDev d;
         double cost;  // per item
@@ -481,11 +510,15 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
         double* g_val = grad ? (double*)e->d_work + 4 : nullptr;
         double* g_slot = grad ? g_val + e->prep.n_paths : nullptr;
         for (const Bucket& b : e->prep.buckets) {
+            if (ov && ov->only_width > 0 && b.D != ov->only_width) continue;
             const int cls = batch_class(b.D), ci = class_index(cls);
+            const Tune& tn = e->tune[b.D];
             int mode = R.F + 1 <= kPrivRows ? 1 : 0;
             if (grad && pair_width(b.D) &&
-                batch_smem_bytes(tile_floats_for(2, R.F), sub, cls) <= class_smem_budget(cls))
-                mode = 2;
+                batch_smem_bytes(tile_floats_for(2, R.F), sub, cls) <= class_smem_budget(cls)) {
+                const int want = ov && ov->mode[b.D] ? ov->mode[b.D] : tn.bt_mode;
+                mode = want == 3 ? 3 : 2;
+            }
             tile_need[ci] = std::max(tile_need[ci], tile_floats_for(mode, R.F));
             const int per_item = item_samples(mode);
             const int n_tiles = (int)((R.M + per_item - 1) / per_item);
@@ -495,7 +528,8 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
             s.d.g_slot = grad ? g_slot + b.slot_base : nullptr;
             s.d.n_paths = b.n_paths;
             s.d.D = b.D;
-            s.d.paths = e->tuned ? e->tune[b.D].bpaths : item_paths(b.D, grad);
+            s.d.paths = ov && ov->paths[b.D] ? ov->paths[b.D]
+                        : tn.bt_paths ? tn.bt_paths : (e->tuned ? tn.bpaths : item_paths(b.D, grad));
             s.d.n_tiles = n_tiles;
             s.d.req = r;
             s.d.priv = mode;
@@ -633,11 +667,13 @@ static thread_local int g_last_batch_kernels = 0;
 
 using namespace qts;
 
-extern "C" qts_status qts_batched_fwd_bwd(int32_t n, const qts_request* reqs, int32_t n_quad,
-                                          qts_stream_t stream) {
+namespace qts {
+
+// Argument checks shared by the batched call and its tuner; grows every
+// request's workspace to what the batched launch needs.
+static qts_status check_batch(int32_t n, const qts_request* reqs, int32_t n_quad, QuadF* qf) {
     if (n < 1 || !reqs) return fail(QTS_ERR_ARG, "no requests");
-    QuadF qf;
-    if (!make_quad(n_quad, &qf, nullptr)) return fail(QTS_ERR_ARG, "n_quad must be in [1, 32]");
+    if (!make_quad(n_quad, qf, nullptr)) return fail(QTS_ERR_ARG, "n_quad must be in [1, 32]");
     for (int r = 0; r < n; ++r) {
         const qts_request& R = reqs[r];
         qts_status st = check_call(R.ens, R.X, R.M, R.F, n_quad);
@@ -656,6 +692,18 @@ extern "C" qts_status qts_batched_fwd_bwd(int32_t n, const qts_request* reqs, in
         qts_status st = ensure_workspace(R.ens, batch_work(R.ens, R.M, R.F, R.grad_phi != nullptr).total);
         if (st != QTS_OK) return st;
     }
+    return QTS_OK;
+}
+
+}  // namespace qts
+
+extern "C" qts_status qts_batched_fwd_bwd(int32_t n, const qts_request* reqs, int32_t n_quad,
+                                          qts_stream_t stream) {
+    QuadF qf;
+    {
+        const qts_status st = check_batch(n, reqs, n_quad, &qf);
+        if (st != QTS_OK) return st;
+    }
     std::vector<uint64_t> key;
     key.push_back((uint64_t)n_quad);
     for (int r = 0; r < n; ++r) {
@@ -664,7 +712,7 @@ extern "C" qts_status qts_batched_fwd_bwd(int32_t n, const qts_request* reqs, in
                            (uint64_t)(uintptr_t)R.grad_phi, (uint64_t)(uintptr_t)R.phi,
                            (uint64_t)(uintptr_t)R.d_leaf, (uint64_t)(uintptr_t)R.d_z,
                            (uint64_t)(uintptr_t)R.ens->d_work, (uint64_t)(uintptr_t)R.ens->d_rec,
-                           (uint64_t)R.ens->tuned})
+                           (uint64_t)R.ens->tune_gen})
             key.push_back(v);
     }
     cudaGraphExec_t exec = nullptr;
@@ -708,6 +756,103 @@ extern "C" qts_status qts_batched_fwd_bwd(int32_t n, const qts_request* reqs, in
     }
     cudaError_t ce = cudaGraphLaunch(exec, (cudaStream_t)stream);
     if (ce != cudaSuccess) return cuda_fail(ce, "graph launch");
+    return QTS_OK;
+}
+
+namespace qts {
+
+// Device time of the persistent kernels of one plan built for `reqs` with the
+// override `ov` (second of two launches); the plan is destroyed afterwards.
+static qts_status time_plan(int n, const qts_request* reqs, const QuadF& qf, const BatchOverride& ov,
+                            cudaStream_t cap, cudaStream_t st, float* ms) {
+    auto* plan = new BatchPlan();
+    qts_status s = build_plan(n, reqs, qf, plan, cap, &ov);
+    cudaError_t ce = cudaSuccess;
+    for (int k = 0; k < 2 && s == QTS_OK && ce == cudaSuccess; ++k) ce = cudaGraphLaunch(plan->exec, st);
+    if (s == QTS_OK && ce == cudaSuccess) ce = cudaEventSynchronize(plan->ev1);
+    if (s == QTS_OK && ce == cudaSuccess) ce = cudaEventElapsedTime(ms, plan->ev0, plan->ev1);
+    if (s == QTS_OK && ce != cudaSuccess) s = cuda_fail(ce, "batched tuning run");
+    cudaStreamSynchronize(st);
+    destroy_plan(plan);
+    return s;
+}
+
+}  // namespace qts
+
+extern "C" qts_status qts_batched_autotune(int32_t n, const qts_request* reqs, int32_t n_quad, int64_t max_samples,
+                                           int32_t* chosen, qts_stream_t stream) {
+    QuadF qf;
+    qts_status st = check_batch(n, reqs, n_quad, &qf);
+    if (st != QTS_OK) return st;
+    if (max_samples < 0) return fail(QTS_ERR_ARG, "max_samples must be >= 0");
+    std::vector<qts_request> sub(reqs, reqs + n);
+    if (max_samples > 0)
+        for (auto& R : sub) R.M = std::min<int64_t>(R.M, max_samples);
+    // work (element-samples) per bucket width of the reduced batch, and whether
+    // the width runs the packed fused pass for some request
+    std::vector<double> work(kMaxD + 1, 0.0);
+    std::vector<char> packed(kMaxD + 1, 0);
+    std::vector<char> fused(kMaxD + 1, 0);
+    for (const auto& R : sub) {
+        if (R.M <= 0) continue;
+        for (const Bucket& b : R.ens->prep.buckets) {
+            if (b.n_paths == 0) continue;
+            work[b.D] += (double)R.M * (double)b.n_paths * b.D;
+            if (R.grad_phi) fused[b.D] = 1;
+            if (R.grad_phi && pair_width(b.D)) packed[b.D] = 1;
+        }
+    }
+    double total = 0.0;
+    for (double w : work) total += w;
+    std::vector<int> widths;
+    for (int D = 1; D <= kMaxD; ++D)
+        if (work[D] > 0.01 * total) widths.push_back(D);  // the rest keep the defaults
+    std::sort(widths.begin(), widths.end(), [&](int a, int b) { return work[a] > work[b]; });
+    cudaStream_t cap;
+    cudaError_t ce = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) return cuda_fail(ce, "capture stream");
+    std::vector<int> best_paths(kMaxD + 1, 0), best_mode(kMaxD + 1, 0);
+    for (int D : widths) {
+        BatchOverride ov;
+        std::memset(&ov, 0, sizeof(ov));
+        ov.only_width = D;
+        const int base = item_paths(D, fused[D] != 0);
+        float best = 1e30f;
+        for (int mode : {2, 3}) {
+            if (mode == 3 && !packed[D]) continue;
+            for (int mult : {1, 2, 4}) {  // base / 2, base, base * 2
+                const int paths = std::max(32, std::min(2048, base * mult / 2 / 32 * 32));
+                ov.paths[D] = paths;
+                ov.mode[D] = packed[D] ? mode : 0;
+                float ms = 0.f;
+                st = time_plan(n, sub.data(), qf, ov, cap, (cudaStream_t)stream, &ms);
+                if (st != QTS_OK) {
+                    cudaStreamDestroy(cap);
+                    return st;
+                }
+                if (ms < best) {
+                    best = ms;
+                    best_paths[D] = paths;
+                    best_mode[D] = ov.mode[D];
+                }
+            }
+        }
+    }
+    cudaStreamDestroy(cap);
+    for (int r = 0; r < n; ++r) {
+        qts_ensemble* e = reqs[r].ens;
+        for (int D : widths) {
+            e->tune[D].bt_paths = best_paths[D];
+            e->tune[D].bt_mode = best_mode[D];
+        }
+        ++e->tune_gen;
+        batch_forget(e);
+    }
+    if (chosen)
+        for (int D = 0; D <= kMaxD; ++D) {
+            chosen[2 * D] = best_paths[D];
+            chosen[2 * D + 1] = best_mode[D];
+        }
     return QTS_OK;
 }
 

@@ -270,7 +270,10 @@ cudaError_t launch_bwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
     a.rec = fp64 ? (const void*)((const Rec64*)e->d_rec + b.rec_off)
                  : (const void*)((const Rec32*)e->d_rec + b.rec_off);
     a.n_paths = b.n_paths;
+    const bool with_phi = phi != nullptr && !fp64;
     a.sub = std::max(1, tn.sub);
+    // wide inputs: stage fewer paths at a time until the block fits shared memory
+    while (a.sub > 1 && bwd_smem_bytes(F, a.sub, b.D, fp64, with_phi) > kSmemMax) a.sub /= 2;
     a.paths_per_block = std::max<int64_t>(a.sub, (int64_t)tn.paths / a.sub * a.sub);
     a.n_tiles = (int)((M + 31) / 32);
     a.X = X;
@@ -287,8 +290,8 @@ cudaError_t launch_bwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
     const int64_t chunks = (b.n_paths + a.paths_per_block - 1) / a.paths_per_block;
     const int64_t blocks = chunks * a.n_tiles;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const bool with_phi = phi != nullptr && !fp64;
     const size_t smem = bwd_smem_bytes(F, a.sub, b.D, fp64, with_phi);
+    if (smem > kSmemMax) return cudaErrorInvalidConfiguration;
     const int warps = std::max(1, std::min(8, tn.warps));
     const int np = b.D <= 8 ? 4 : 2;
     switch (b.D) {

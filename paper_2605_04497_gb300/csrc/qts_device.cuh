@@ -15,6 +15,9 @@ namespace qts {
 // walk (fixed sample, consecutive rows) conflict-free as well.
 constexpr int kTileLd = 33;
 
+// The most dynamic shared memory one block may use on sm_103a (227 KB).
+constexpr size_t kSmemMax = 227 * 1024;
+
 // A wait is declared failed after about kWaitNs of GPU time (the global
 // nanosecond timer), or after kWaitLimit polls as a backstop (each try_wait
 // may suspend for a hardware-defined interval).

@@ -34,6 +34,8 @@ struct FwdArgs {
     int ntiles;         // sample tiles of 32 per block: 1 (warps share the tile and
                         // split paths, atomics) or the warp count (each warp owns a
                         // tile and walks every path; private phi tile, no atomics)
+    int gphi;           // FP64 only: 1 = no accumulator tile (it would not fit shared
+                        // memory), contributions go straight to phi with FP64 atomics
     QuadF q;
     QuadD qd;
 };
@@ -47,8 +49,8 @@ cudaError_t launch_fwd_d(const FwdArgs& a, int np, bool fp64, int warps, int64_t
 // --------------------------------------------------------------- kernel ---
 
 template <typename Rec, typename Acc>
-__device__ __forceinline__ size_t fwd_smem_layout(int F, int sub, int D, int ntiles, float** xs, Acc** ps,
-                                                  Rec** stage0, Rec** stage1, uint64_t** bars,
+__device__ __forceinline__ size_t fwd_smem_layout(int F, int sub, int D, int ntiles, bool gphi, float** xs,
+                                                  Acc** ps, Rec** stage0, Rec** stage1, uint64_t** bars,
                                                   unsigned char* base) {
     const int rows = F + 1;
     size_t off = 0;
@@ -56,7 +58,7 @@ __device__ __forceinline__ size_t fwd_smem_layout(int F, int sub, int D, int nti
     off += (size_t)ntiles * rows * kTileLd * sizeof(float);
     off = (off + 15) & ~(size_t)15;
     *ps = (Acc*)(base + off);
-    off += (size_t)ntiles * rows * kTileLd * sizeof(Acc);
+    if (!gphi) off += (size_t)ntiles * rows * kTileLd * sizeof(Acc);
     off = (off + 15) & ~(size_t)15;
     *stage0 = (Rec*)(base + off);
     off += (size_t)sub * (D + 1) * sizeof(Rec);
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
     Acc* ps;
     Rec *st0, *st1;
     uint64_t* bars;
-    fwd_smem_layout<Rec, Acc>(a.F, a.sub, D, a.ntiles, &xs, &ps, &st0, &st1, &bars, smem);
+    fwd_smem_layout<Rec, Acc>(a.F, a.sub, D, a.ntiles, a.gphi != 0, &xs, &ps, &st0, &st1, &bars, smem);
     __shared__ int s_flag;
     __shared__ uint32_t s_phase[2];
 
@@ -100,7 +102,8 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
         mbar_fence_init();
         s_phase[0] = s_phase[1] = 0;
     }
-    for (int idx = threadIdx.x; idx < a.ntiles * stride; idx += blockDim.x) ps[idx] = (Acc)0;
+    if (!a.gphi)
+        for (int idx = threadIdx.x; idx < a.ntiles * stride; idx += blockDim.x) ps[idx] = (Acc)0;
     // sample tiles (row = feature, column = sample) plus a zero row F for padding
     const bool has_nan = load_tiles_t(xs, a.X, s0, a.M, F, F, 1, a.ntiles, stride) || a.cat != 0;
 
@@ -108,8 +111,16 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
         (const Rec*)a.rec, p0, p1, a.sub, st0, st1, bars, s_phase, &s_flag, a.status,
         [&](int64_t, const Rec* r) {
             if constexpr (FP64) {
-                if (has_nan) fwd_path_f64<D, true>(r, my_xs, my_ps, lane, a.qd);
-                else fwd_path_f64<D, false>(r, my_xs, my_ps, lane, a.qd);
+                if (a.gphi) {
+                    // this lane's row of phi (lanes past M only skip their adds)
+                    const bool live = sw + lane < a.M;
+                    double* row = a.phi + (live ? (sw + lane) * (F + 1) : 0);
+                    if (has_nan) fwd_path_f64<D, true>(r, my_xs, row, lane, a.qd, F, live);
+                    else fwd_path_f64<D, false>(r, my_xs, row, lane, a.qd, F, live);
+                } else {
+                    if (has_nan) fwd_path_f64<D, true>(r, my_xs, my_ps, lane, a.qd);
+                    else fwd_path_f64<D, false>(r, my_xs, my_ps, lane, a.qd);
+                }
             } else {
                 const SmemCols xr{my_xs, lane};
                 if (priv) {
@@ -122,7 +133,7 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
             }
         },
         priv);
-    if (!ok) return;
+    if (!ok || a.gphi) return;
     const int nflush = 32 * F;
     if (priv) {
         for (int idx = lane; idx < nflush; idx += 32) {
@@ -214,11 +225,11 @@ cudaError_t launch_phi_init(double* phi, int64_t M, int F, double bias, cudaStre
     return cudaGetLastError();
 }
 
-size_t fwd_smem_bytes(int F, int sub, int D, bool fp64, int ntiles) {
+size_t fwd_smem_bytes(int F, int sub, int D, bool fp64, int ntiles, bool gphi = false) {
     const size_t rows = F + 1;
     size_t off = ntiles * rows * kTileLd * 4;
     off = (off + 15) & ~(size_t)15;
-    off += ntiles * rows * kTileLd * (fp64 ? 8 : 4);
+    if (!gphi) off += ntiles * rows * kTileLd * (fp64 ? 8 : 4);
     off = (off + 15) & ~(size_t)15;
     off += 2 * (size_t)sub * (D + 1) * (fp64 ? sizeof(Rec64) : sizeof(Rec32));
     off = (off + 15) & ~(size_t)15;
@@ -235,10 +246,19 @@ cudaError_t launch_fwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
                  : (const void*)((const Rec32*)e->d_rec + b.rec_off);
     a.n_paths = b.n_paths;
     a.sub = std::max(1, tn.sub);
-    a.paths_per_block = std::max<int64_t>(a.sub, (int64_t)tn.paths / a.sub * a.sub);
     const int warps = std::max(1, std::min(8, tn.warps));
     // private tiles when the per-warp X and phi tiles stay small
     a.ntiles = (!fp64 && tn.priv && fwd_smem_bytes(F, a.sub, b.D, false, warps) <= 100 * 1024) ? warps : 1;
+    // wide inputs: stage fewer paths at a time, and (FP64) drop the accumulator
+    // tile for direct FP64 atomics into phi, until the block fits shared memory
+    a.gphi = 0;
+    while (a.sub > 1 && fwd_smem_bytes(F, a.sub, b.D, fp64, a.ntiles) > kSmemMax) a.sub /= 2;
+    if (fp64 && fwd_smem_bytes(F, a.sub, b.D, fp64, a.ntiles) > kSmemMax) {
+        a.gphi = 1;
+        a.sub = std::max(1, tn.sub);
+        while (a.sub > 1 && fwd_smem_bytes(F, a.sub, b.D, fp64, a.ntiles, true) > kSmemMax) a.sub /= 2;
+    }
+    a.paths_per_block = std::max<int64_t>(a.sub, (int64_t)tn.paths / a.sub * a.sub);
     a.n_tiles = (int)((M + 32 * a.ntiles - 1) / (32 * a.ntiles));
     a.X = X;
     a.M = M;
@@ -251,8 +271,8 @@ cudaError_t launch_fwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
     const int64_t chunks = (b.n_paths + a.paths_per_block - 1) / a.paths_per_block;
     const int64_t blocks = chunks * a.n_tiles;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const size_t smem = fwd_smem_bytes(F, a.sub, b.D, fp64, a.ntiles);
-    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    const size_t smem = fwd_smem_bytes(F, a.sub, b.D, fp64, a.ntiles, a.gphi != 0);
+    if (smem > kSmemMax) return cudaErrorInvalidConfiguration;
     switch (b.D) {
 #define QTS_CASE(DD) \
     case DD: return launch_fwd_d<DD>(a, tn.np, fp64, warps, blocks, smem, st);

@@ -293,6 +293,8 @@ cudaError_t launch_int_bucket(const qts_ensemble* e, const Bucket& b, const floa
     a.rec = (const Rec32*)e->d_rec + b.rec_off;
     a.n_paths = b.n_paths;
     a.sub = b.D <= 16 ? 16 : 8;
+    // wide inputs: stage fewer paths at a time until the block fits shared memory
+    while (a.sub > 1 && int_smem_bytes(F, a.sub, b.D, false) > kSmemMax) a.sub /= 2;
     a.paths_per_block = std::max<int64_t>(a.sub, 512 / a.sub * a.sub);
     a.n_tiles = (int)((M + 31) / 32);
     a.X = X;
@@ -306,7 +308,7 @@ cudaError_t launch_int_bucket(const qts_ensemble* e, const Bucket& b, const floa
     a.q = q;
     bool pair_smem = int_smem_bytes(F, a.sub, b.D, true) <= kSmemBudget;
     const size_t smem = int_smem_bytes(F, a.sub, b.D, pair_smem);
-    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    if (smem > kSmemMax) return cudaErrorInvalidConfiguration;
     const int64_t chunks = (b.n_paths + a.paths_per_block - 1) / a.paths_per_block;
     const int64_t blocks = chunks * a.n_tiles;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;

@@ -108,6 +108,10 @@ struct Tune {
     int np = 8;           // nodes per register pass (8, 4 or 2)
     int bpaths = 128;     // paths per work item of the fused forward + adjoint pass
     int priv = 1;         // forward: let each warp own a sample tile when it fits
+    // choices of the batched-launch tuner (0: not tuned, the launch's default)
+    int bt_paths = 0;     // paths per work item of the persistent batched kernel
+    int bt_mode = 0;      // sample mapping of the packed fused pass: 2 (64 samples
+                          // per warp) or 3 (64 samples shared by the block's warps)
 };
 
 }  // namespace qts
@@ -151,6 +155,7 @@ struct qts_ensemble {
     // per-width launch tuning (index = bucket width)
     qts::Tune tune[qts::kMaxD + 1];
     bool tuned = false;
+    uint32_t tune_gen = 0;            // bumped by every tuning call (cached batched graphs key on it)
 };
 
 namespace qts {

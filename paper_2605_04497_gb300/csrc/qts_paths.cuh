@@ -96,9 +96,13 @@ __device__ __forceinline__ void fwd_path_f32(const Rec32* __restrict__ r, const 
 }
 
 
+// ps: the block's FP64 accumulator tile [feature][kTileLd] (column = lane), or,
+// with global_F = F > 0 (the tile does not fit shared memory), this lane's row
+// of the FP64 output itself; lanes past the last sample pass live = false.
 template <int D, bool HAS_NAN>
 __device__ __forceinline__ void fwd_path_f64(const Rec64* __restrict__ r, const float* __restrict__ xs,
-                                             double* ps, int lane, const QuadD& q) {
+                                             double* ps, int lane, const QuadD& q, int global_F = 0,
+                                             bool live = true) {
     const double val = r[0].z;
     double dd[D], zz[D], cacc[D];
     int ff[D];
@@ -129,8 +133,15 @@ __device__ __forceinline__ void fwd_path_f64(const Rec64* __restrict__ r, const 
             S *= A[j];
         }
     }
+    if (!live) return;
+    if (global_F == 0) {
 #pragma unroll
-    for (int j = 0; j < D; ++j) atomicAdd(&ps[ff[j] * kTileLd + lane], dd[j] * cacc[j]);
+        for (int j = 0; j < D; ++j) atomicAdd(&ps[ff[j] * kTileLd + lane], dd[j] * cacc[j]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+            if (ff[j] < global_F) atomicAdd(&ps[ff[j]], dd[j] * cacc[j]);  // padding elements carry feature F
+    }
 }
 
 

@@ -133,7 +133,10 @@ extern "C" qts_status qts_autotune(qts_ensemble* e, const float* X, int64_t M, i
         const std::string key = cache_key(b.D, F, M);
         auto it = cache.find(key);
         if (it != cache.end()) {
+            const Tune keep = e->tune[b.D];  // the batched-launch tuner's choices stay
             e->tune[b.D] = it->second;
+            e->tune[b.D].bt_paths = keep.bt_paths;
+            e->tune[b.D].bt_mode = keep.bt_mode;
             continue;
         }
         Tune best = e->tune[b.D];
@@ -190,6 +193,7 @@ extern "C" qts_status qts_autotune(qts_ensemble* e, const float* X, int64_t M, i
     cudaFree(grad);
     if (ce != cudaSuccess) return cuda_fail(ce, "autotune");
     e->tuned = true;
+    ++e->tune_gen;
     batch_forget(e);
     if (cache_path) write_cache(cache_path, cache);
     return QTS_OK;

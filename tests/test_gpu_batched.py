@@ -145,3 +145,28 @@ def test_autotune_keeps_results_and_writes_cache(qts, tmp_path):
     assert rel_err_rows(again, before).max() <= 1e-6
     E.close()
     E2.close()
+
+
+def test_batched_autotune_keeps_results(qts):
+    """The batched-launch tuner changes only launch parameters: after tuning,
+    phi and the gradients still match the oracle, and a later call rebuilds
+    its graph with the tuned values."""
+    import torch
+
+    works = hetero_batch(6, seed=5151)
+    items = _prepare(qts, works)
+    reqs = qts.make_requests(items)
+    chosen = qts.batched_autotune(reqs, 8, max_samples=64)
+    assert chosen, "some width must carry 1% of the work"
+    for D, (paths, mode) in chosen.items():
+        assert paths >= 32 and mode in (0, 2, 3), (D, paths, mode)
+    qts.batched_fwd_bwd(reqs)
+    torch.cuda.synchronize()
+    for w, it in zip(works, items):
+        it["ens"].sync_status()
+        assert rel_err_rows(it["phi"].cpu().numpy(), oracle.shap_exact(w.ens, w.X)).max() <= TOL32, w.name
+        dl_ref, dz_ref = oracle.grad_exact(w.ens, w.X, w.grad_phi)
+        assert rel(it["d_leaf"].cpu().numpy(), dl_ref) <= TOL32, w.name
+        assert rel(it["d_z"].cpu().numpy(), dz_ref) <= TOL32, w.name
+    for it in items:
+        it["ens"].close()

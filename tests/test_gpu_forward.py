@@ -214,3 +214,21 @@ def test_deep_depth20_sampled(qts):
     ref = oracle.shap_exact(w.ens, w.X[:24])
     assert rel_err_rows(phi[:24], ref).max() <= TOL32
     E.close()
+
+
+def test_deep_depth20_full_size_sampled_rows(qts):
+    """The 200-tree depth-20 workload at full size (F = 24, M = 5,000, 6.8 M
+    merged paths up to 19 unique features) on 16 rows spread over the batch,
+    against the oracle's exact expansion; paths beyond 16 unique features carry
+    the 8-point rule's quadrature error (Thm 2), which stays far below 1e-5."""
+    import torch
+
+    w = synth.workload("deep-depth20")
+    E = qts.Ensemble.from_arrays(w.ens)
+    assert E.info()["max_unique"] > 16
+    phi = qts.shap_values(E, torch.from_numpy(w.X).cuda()).cpu().numpy()
+    E.sync_status()
+    E.close()
+    rows = np.r_[0:4, 2500:2504, 4992:5000]
+    ref = oracle.shap_exact(w.ens, w.X[rows])
+    assert rel_err_rows(phi[rows], ref).max() <= TOL32

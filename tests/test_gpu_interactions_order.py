@@ -44,6 +44,23 @@ def scale_of(ens, X):
     return np.maximum(np.abs(phi.sum(1)), np.abs(phi[:, :-1]).max(1))
 
 
+@pytest.mark.parametrize("order", [7, 8])
+def test_orders_7_and_8_against_exact_expansion(qts, order):
+    """The two highest orders the entry point accepts: depth 10 over F = 9, so
+    paths reach 8 unique features and order 8 is not identically zero."""
+    ens = tiny_ensemble(2707, n_trees=4, depth=10, F=9, n_train=3000)
+    X = synth.normal(2707, 1, (45, 9))
+    E = qts.Ensemble.from_arrays(ens)
+    assert E.info()["max_unique"] >= order
+    got = qts.shap_interactions_order(E, cuda(X), order).cpu().numpy().astype(np.float64)
+    E.sync_status()
+    E.close()
+    ref = oracle.sii_order_exact(ens, X, order)
+    assert np.abs(ref).max() > 0
+    err = np.abs(got - ref).max(axis=1) / scale_of(ens, X)
+    assert err.max() <= TOL32, (order, err.max())
+
+
 @pytest.mark.parametrize("order", [2, 3, 4, 5, 6])
 def test_against_exact_expansion(qts, order):
     """depth 9 over F = 8 (repeated features, paths up to 8 unique features),

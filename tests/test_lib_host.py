@@ -250,7 +250,7 @@ def test_host_rejects_malformed_models():
         assert e.value.status == status, (e.value.status, str(e.value))
 
     big = ens.copy()
-    big.n_features = 641
+    big.n_features = 833  # one above QTS_MAX_FEATURES
     expect(big, 4)
     expect(big, 4, qts.describe_paths)
     bad = ens.copy()
