@@ -18,6 +18,10 @@ constexpr int kTileLd = 33;
 // The most dynamic shared memory one block may use on sm_103a (227 KB).
 constexpr size_t kSmemMax = 227 * 1024;
 
+// Calls with at most this many samples map lanes to (path, sample) pairs
+// instead of one sample per lane (which would leave most lanes idle).
+constexpr int kFewRows = 16;
+
 // A wait is declared failed after about kWaitNs of GPU time (the global
 // nanosecond timer), or after kWaitLimit polls as a backstop (each try_wait
 // may suspend for a hardware-defined interval).
@@ -132,17 +136,16 @@ namespace qts {
 // Block-level path streaming.  The block's path range [p0, p1) of one bucket
 // (D elements + 1 header record per path) is copied into two shared staging
 // buffers of `sub` paths each by bulk copies, double-buffered on two
-// mbarriers; warp w calls body(global_path_index, records) for paths
-// w, w + nwarps, ... of each staged sub-chunk (every path, when every_warp).  Thread 0 does the bounded wait
-// and broadcasts the outcome, so the decision to stop is block-uniform.
-// Returns false (after reporting QTS_ERR_TIMEOUT and waiting, bounded, for the
-// copies in flight) if a copy did not complete.  Must be called by all threads;
-// `bars` must have been initialised by mbar_init(.., 1) and a __syncthreads.
-template <typename Rec, int D, typename Body>
-__device__ __forceinline__ bool stream_paths(const Rec* __restrict__ rec, int64_t p0, int64_t p1, int sub,
-                                             Rec* st0, Rec* st1, uint64_t* bars, uint32_t* phase_base,
-                                             int* s_flag, int* status, Body&& body, bool every_warp = false) {
-    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+// mbarriers; visit(first_path_index, count, records) runs on every thread for
+// each staged sub-chunk.  Thread 0 does the bounded wait and broadcasts the
+// outcome, so the decision to stop is block-uniform.  Returns false (after
+// reporting QTS_ERR_TIMEOUT and waiting, bounded, for the copies in flight) if
+// a copy did not complete.  Must be called by all threads; `bars` must have
+// been initialised by mbar_init(.., 1) and a __syncthreads.
+template <typename Rec, int D, typename Visit>
+__device__ __forceinline__ bool stream_chunks(const Rec* __restrict__ rec, int64_t p0, int64_t p1, int sub,
+                                              Rec* st0, Rec* st1, uint64_t* bars, uint32_t* phase_base,
+                                              int* s_flag, int* status, Visit&& visit) {
     const int nsub = (int)((p1 - p0 + sub - 1) / sub);
     // phase_base[k] counts completed phases of barrier k before this call, so
     // the driver can be called repeatedly (persistent kernels) on the same bars
@@ -165,9 +168,7 @@ __device__ __forceinline__ bool stream_paths(const Rec* __restrict__ rec, int64_
         (void)mbar_try_wait(&bars[c & 1], parity);  // acquire the bulk-copy writes
         const Rec* buf = (c & 1) ? st1 : st0;
         const int64_t q0 = p0 + (int64_t)c * sub;
-        const int cnt = (int)imin64(sub, p1 - q0);
-        const int i0 = every_warp ? 0 : warp, di = every_warp ? 1 : nwarps;
-        for (int i = i0; i < cnt; i += di) body(q0 + i, buf + i * (D + 1));
+        visit(q0, (int)imin64(sub, p1 - q0), buf);
         __syncthreads();
         if (threadIdx.x == 0 && c + 2 < nsub) issue(c + 2);
     }
@@ -187,6 +188,40 @@ __device__ __forceinline__ bool stream_paths(const Rec* __restrict__ rec, int64_
     }
     __syncthreads();
     return true;
+}
+
+// Lane = sample: warp w calls body(global_path_index, records) for paths w,
+// w + nwarps, ... of each staged sub-chunk (every path, when every_warp).
+template <typename Rec, int D, typename Body>
+__device__ __forceinline__ bool stream_paths(const Rec* __restrict__ rec, int64_t p0, int64_t p1, int sub,
+                                             Rec* st0, Rec* st1, uint64_t* bars, uint32_t* phase_base,
+                                             int* s_flag, int* status, Body&& body, bool every_warp = false) {
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    return stream_chunks<Rec, D>(rec, p0, p1, sub, st0, st1, bars, phase_base, s_flag, status,
+                                 [&](int64_t q0, int cnt, const Rec* buf) {
+                                     const int i0 = every_warp ? 0 : warp, di = every_warp ? 1 : nwarps;
+                                     for (int i = i0; i < cnt; i += di) body(q0 + i, buf + i * (D + 1));
+                                 });
+}
+
+// Lane = (path, sample), for calls with few samples: warp w takes `group`
+// consecutive paths of [p0, p1) at a time (paths p0 + w group, then every
+// nwarps * group), and the lanes of slot k < group work on its k-th path,
+// reading the records straight from global memory (each lane its own path:
+// no shared staging).  Every lane calls body(global_path_index, records,
+// valid); a lane without a path (slot >= group, or past the end) gets the
+// step's first path with valid = false and must not write results.  The trip
+// count is the same on every lane of a warp, so body may use __syncwarp.
+template <typename Rec, int D, typename Body>
+__device__ __forceinline__ void walk_paths_grouped(const Rec* __restrict__ rec, int64_t p0, int64_t p1, int group,
+                                                   int slot, Body&& body) {
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int64_t i = p0 + (int64_t)warp * group; i < p1; i += (int64_t)nwarps * group) {
+        const int64_t k = i + slot;
+        const bool valid = slot < group && k < p1;
+        const int64_t use = valid ? k : i;
+        body(use, rec + use * (D + 1), valid);
+    }
 }
 
 // Transposed tile of 32 rows of a row-major matrix: tile[c * kTileLd + s] =

@@ -36,6 +36,8 @@ struct FwdArgs {
                         // tile and walks every path; private phi tile, no atomics)
     int gphi;           // FP64 only: 1 = no accumulator tile (it would not fit shared
                         // memory), contributions go straight to phi with FP64 atomics
+    int group;          // few samples (M <= 16): lanes are (path, sample) pairs, a warp
+                        // takes `group` = 32 / M paths at a time (FP32 only); 0 otherwise
     QuadF q;
     QuadD qd;
 };
@@ -107,7 +109,23 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
     // sample tiles (row = feature, column = sample) plus a zero row F for padding
     const bool has_nan = load_tiles_t(xs, a.X, s0, a.M, F, F, 1, a.ntiles, stride) || a.cat != 0;
 
-    const bool ok = stream_paths<Rec, D>(
+    bool ok;
+    if (!FP64 && a.group > 0) {
+        // few samples: lane (slot, sample) evaluates path slot of each group for
+        // its sample (column of the tile); the shared phi tile takes atomics
+        const int slot = lane / (int)a.M, col = lane - slot * (int)a.M;
+        walk_paths_grouped<Rec, D>((const Rec*)a.rec, p0, p1, a.group, slot, [&](int64_t, const Rec* r, bool valid) {
+            if constexpr (!FP64) {
+                if (!valid) return;
+                const SmemCols xr{xs, col};
+                if (has_nan) fwd_path_f32<D, NP, true, SmemCols, kPhiAtomic>(r, xr, ps, col, a.q);
+                else fwd_path_f32<D, NP, false, SmemCols, kPhiAtomic>(r, xr, ps, col, a.q);
+            }
+        });
+        ok = true;
+        __syncthreads();  // every warp's adds are in the tile before the flush
+    } else {
+    ok = stream_paths<Rec, D>(
         (const Rec*)a.rec, p0, p1, a.sub, st0, st1, bars, s_phase, &s_flag, a.status,
         [&](int64_t, const Rec* r) {
             if constexpr (FP64) {
@@ -133,6 +151,7 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
             }
         },
         priv);
+    }
     if (!ok || a.gphi) return;
     const int nflush = 32 * F;
     if (priv) {
@@ -249,6 +268,8 @@ cudaError_t launch_fwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
     const int warps = std::max(1, std::min(8, tn.warps));
     // private tiles when the per-warp X and phi tiles stay small
     a.ntiles = (!fp64 && tn.priv && fwd_smem_bytes(F, a.sub, b.D, false, warps) <= 100 * 1024) ? warps : 1;
+    a.group = (!fp64 && M <= kFewRows) ? (int)(32 / M) : 0;
+    if (a.group) a.ntiles = 1;
     // wide inputs: stage fewer paths at a time, and (FP64) drop the accumulator
     // tile for direct FP64 atomics into phi, until the block fits shared memory
     a.gphi = 0;
@@ -259,6 +280,7 @@ cudaError_t launch_fwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
         while (a.sub > 1 && fwd_smem_bytes(F, a.sub, b.D, fp64, a.ntiles, true) > kSmemMax) a.sub /= 2;
     }
     a.paths_per_block = std::max<int64_t>(a.sub, (int64_t)tn.paths / a.sub * a.sub);
+    if (a.group) a.paths_per_block = std::max<int64_t>(a.paths_per_block, 4LL * warps * a.group);
     a.n_tiles = (int)((M + 32 * a.ntiles - 1) / (32 * a.ntiles));
     a.X = X;
     a.M = M;

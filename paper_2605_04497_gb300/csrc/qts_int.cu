@@ -43,6 +43,8 @@ struct IntArgs {
     int F;
     int cat;            // ensemble has categorical elements: always the NaN-aware variant
     int64_t n_pairs;
+    int group;          // few samples (M <= 16): lanes are (path, sample) pairs, a warp
+                        // takes `group` = 32 / M paths at a time; 0 otherwise
     double* acc_pair;   // [n_pairs][M]
     double* acc_phi;    // [F][M]
     int* status;
@@ -177,12 +179,26 @@ __global__ void __launch_bounds__(256) int_kernel(IntArgs a) {
     const bool has_nan = load_tile_t(xs, a.X, s0, a.M, F, F, 1) || a.cat != 0;
     const int64_t s = s0 + lane;
 
-    const bool ok = stream_paths<Rec32, D>(
-        a.rec, p0, p1, a.sub, st0, st1, bars, s_phase, &s_flag, a.status,
-        [&](int64_t, const Rec32* r) {
-            if (has_nan) int_path_f32<D, NP, true, PAIR_SMEM>(r, xs, ps, pt, a.acc_pair, s, a.M, lane, F, a.q);
-            else int_path_f32<D, NP, false, PAIR_SMEM>(r, xs, ps, pt, a.acc_pair, s, a.M, lane, F, a.q);
+    bool ok;
+    if (a.group > 0) {
+        // few samples: lane (slot, sample) evaluates path slot of each group for
+        // its sample (tile column); the pair and phi tiles take atomics anyway
+        const int slot = lane / (int)a.M, col = lane - slot * (int)a.M;
+        walk_paths_grouped<Rec32, D>(a.rec, p0, p1, a.group, slot, [&](int64_t, const Rec32* r, bool valid) {
+            if (!valid) return;
+            if (has_nan) int_path_f32<D, NP, true, PAIR_SMEM>(r, xs, ps, pt, a.acc_pair, col, a.M, col, F, a.q);
+            else int_path_f32<D, NP, false, PAIR_SMEM>(r, xs, ps, pt, a.acc_pair, col, a.M, col, F, a.q);
         });
+        ok = true;
+        __syncthreads();  // every warp's adds are in the tiles before the flush
+    } else {
+        ok = stream_paths<Rec32, D>(
+            a.rec, p0, p1, a.sub, st0, st1, bars, s_phase, &s_flag, a.status,
+            [&](int64_t, const Rec32* r) {
+                if (has_nan) int_path_f32<D, NP, true, PAIR_SMEM>(r, xs, ps, pt, a.acc_pair, s, a.M, lane, F, a.q);
+                else int_path_f32<D, NP, false, PAIR_SMEM>(r, xs, ps, pt, a.acc_pair, s, a.M, lane, F, a.q);
+            });
+    }
     if (!ok) return;
     // flush: consecutive threads take consecutive samples of one row, so the
     // FP64 adds into the [row][sample] accumulators are coalesced
@@ -296,7 +312,9 @@ cudaError_t launch_int_bucket(const qts_ensemble* e, const Bucket& b, const floa
     // wide inputs: stage fewer paths at a time until the block fits shared memory
     while (a.sub > 1 && int_smem_bytes(F, a.sub, b.D, false) > kSmemMax) a.sub /= 2;
     a.paths_per_block = std::max<int64_t>(a.sub, 512 / a.sub * a.sub);
+    if (a.group) a.paths_per_block = std::max<int64_t>(a.paths_per_block, 4LL * 4 * a.group);
     a.n_tiles = (int)((M + 31) / 32);
+    a.group = M <= kFewRows ? (int)(32 / M) : 0;
     a.X = X;
     a.M = M;
     a.F = F;

@@ -258,6 +258,9 @@ extern "C" qts_status qts_shap_interactions3(qts_ensemble* e, const float* X, in
     if (F > QTS_MAX_FEATURES_ORDER3)
         return fail(QTS_ERR_UNSUPPORTED, "third-order interactions support at most " +
                                              std::to_string(QTS_MAX_FEATURES_ORDER3) + " features");
+    // few samples: the any-order kernel maps lanes to (path, sample) pairs and
+    // writes the same compact layout
+    if (M <= kFewRows) return qts_shap_interactions_order(e, X, M, F, 3, n_quad, sii3, stream);
     cudaStream_t s = (cudaStream_t)stream;
     QuadF qf;
     if (!make_quad(n_quad, &qf, nullptr)) return fail(QTS_ERR_ARG, "quadrature rule");

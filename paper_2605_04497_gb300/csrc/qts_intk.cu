@@ -46,6 +46,8 @@ struct IntkArgs {
     int F;
     int cat;            // ensemble has categorical elements: always the NaN-aware variant
     int order;
+    int group;          // few samples (M <= 16): lanes are (path, sample) pairs, a warp
+                        // takes `group` = 32 / M paths at a time; 0 otherwise
     double* acc;        // [C(F, order)][M]
     int* status;
     QuadF q;
@@ -56,7 +58,8 @@ struct IntkPath {
     const Rec32* r;     // the path's records (header, elements) in shared memory
     const float* dd;    // [element][32] d = o - z of the lane's sample
     const float2* S;    // [element][pair][32] suffix products at this pass's nodes
-    const int* fe;      // [element] feature (warp-uniform)
+    const int* fe;      // feature of element j at fe[j * fe_ld] (fe_ld 1: warp-uniform;
+    int fe_ld;          // 32: this lane's own path, when lanes hold different paths)
     float2 T[kIntkPairs];  // this pass's nodes
     int nreal;          // elements with a real feature (padding excluded)
     int F;
@@ -80,7 +83,7 @@ __host__ __device__ __forceinline__ IntkSmem intk_smem(int F, int sub, int D) {
     L.S = 0;
     L.dd = align16(L.S + (size_t)kIntkWarps * kIntkMaxD * kIntkPairs * 32 * sizeof(float2));
     L.fe = align16(L.dd + (size_t)kIntkWarps * kIntkMaxD * 32 * sizeof(float));
-    L.xs = align16(L.fe + (size_t)kIntkWarps * kIntkMaxD * sizeof(int));
+    L.xs = align16(L.fe + (size_t)kIntkWarps * kIntkMaxD * 32 * sizeof(int));
     L.st = align16(L.xs + (size_t)(F + 1) * kTileLd * sizeof(float));
     L.bars = align16(L.st + 2 * (size_t)sub * (D + 1) * sizeof(Rec32));
     L.total = L.bars + 2 * sizeof(uint64_t);
@@ -103,7 +106,7 @@ __device__ __forceinline__ void intk_choose(const IntkPath& c, int start, const 
     for (int k = 0; k < kIntkPairs; ++k) R[k] = R0[k];
 #pragma unroll 1
     for (int j = start; j + REM < c.nreal; ++j) {
-        const int f = c.fe[j];
+        const int f = c.fe[j * c.fe_ld];
         const float d = c.dd[j * 32 + c.lane];
         // subsets that agree so far and take a smaller feature here come first
         const int64_t rk = rank + binom_r<REM + 1>(c.F - prev - 1) - binom_r<REM + 1>(c.F - f);
@@ -123,23 +126,29 @@ __device__ __forceinline__ void intk_choose(const IntkPath& c, int start, const 
     }
 }
 
+// lane: the lane's slot in the per-warp dd / S / fe arrays; col: its sample's
+// column of the x tile; grouped: lanes hold different paths (r is per lane,
+// features go to fe[j * 32 + lane]); live = false: compute, do not add.
 template <int D, bool HAS_NAN>
 __device__ __forceinline__ void intk_path(const Rec32* __restrict__ r, const float* __restrict__ xs, float* dd,
-                                          float2* S, int* fe, const IntkArgs& a, int64_t s, int lane) {
+                                          float2* S, int* fe, const IntkArgs& a, int64_t s, int lane, int col,
+                                          bool grouped, bool live) {
     const int F = a.F;
     int nreal = D;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
         const Rec32 e = r[1 + j];
         const int f = feat_of(e.bits);
-        const bool o = satisfies<HAS_NAN>(xs[f * kTileLd + lane], e.lo, e.hi, e.bits);
+        const bool o = satisfies<HAS_NAN>(xs[f * kTileLd + col], e.lo, e.hi, e.bits);
         dd[j * 32 + lane] = (o ? 1.f : 0.f) - e.z;
-        if (lane == 0) fe[j] = f;
+        if (grouped) fe[j * 32 + lane] = f;
+        else if (lane == 0) fe[j] = f;
         if (f >= F && j < nreal) nreal = j;
     }
     __syncwarp();
-    if (nreal >= a.order) {
-        IntkPath c{r, dd, S, fe, {}, nreal, F, lane, s < a.M, s, a.M, a.acc};
+    if (nreal >= a.order) {  // widths <= 16 have no padding: the same on every lane
+        IntkPath c{r, dd, S, grouped ? fe + lane : fe, grouped ? 32 : 1, {}, nreal, F, lane, live && s < a.M, s,
+                   a.M, a.acc};
         const float val = r[0].z;
         for (int m0 = 0; m0 < a.q.n_pad; m0 += 2 * kIntkPairs) {
             float2 R0[kIntkPairs], suf[kIntkPairs];
@@ -204,11 +213,21 @@ __global__ void __launch_bounds__(kIntkWarps * 32) intk_kernel(IntkArgs a) {
     const int64_t s = s0 + lane;
     float2* S = S_all + (size_t)warp * kIntkMaxD * kIntkPairs * 32;
     float* dd = dd_all + (size_t)warp * kIntkMaxD * 32;
-    int* fe = fe_all + (size_t)warp * kIntkMaxD;
+    int* fe = fe_all + (size_t)warp * kIntkMaxD * 32;
+    if (a.group > 0) {
+        // few samples: lane (slot, sample) evaluates path slot of each group for
+        // its sample; lanes without a path follow along without adding
+        const int slot = lane / (int)a.M, col = lane - slot * (int)a.M;
+        walk_paths_grouped<Rec32, D>(a.rec, p0, p1, a.group, slot, [&](int64_t, const Rec32* r, bool valid) {
+            if (has_nan) intk_path<D, true>(r, xs, dd, S, fe, a, col, lane, col, true, valid);
+            else intk_path<D, false>(r, xs, dd, S, fe, a, col, lane, col, true, valid);
+        });
+        return;
+    }
     (void)stream_paths<Rec32, D>(a.rec, p0, p1, a.sub, st0, st1, bars, s_phase, &s_flag, a.status,
                                  [&](int64_t, const Rec32* r) {
-                                     if (has_nan) intk_path<D, true>(r, xs, dd, S, fe, a, s, lane);
-                                     else intk_path<D, false>(r, xs, dd, S, fe, a, s, lane);
+                                     if (has_nan) intk_path<D, true>(r, xs, dd, S, fe, a, s, lane, lane, false, true);
+                                     else intk_path<D, false>(r, xs, dd, S, fe, a, s, lane, lane, false, true);
                                  });
 }
 
@@ -275,6 +294,8 @@ static cudaError_t launch_intk_bucket(const qts_ensemble* e, const Bucket& b, co
     a.sub = 16;
     a.paths_per_block = 128;
     a.n_tiles = (int)((M + 31) / 32);
+    a.group = M <= kFewRows ? (int)(32 / M) : 0;
+    if (a.group) a.paths_per_block = std::max<int64_t>(a.paths_per_block, 4LL * kIntkWarps * a.group);
     a.X = X;
     a.M = M;
     a.F = F;
