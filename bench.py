@@ -205,6 +205,11 @@ def run_ours(args, rank, world, local):
     ens = [qts.Ensemble.from_arrays(w.ens) for w in works]
     log(f"prepared path tables in {time.time() - t0:.1f}s")
     infos = [e.info() for e in ens]
+    # the tables the batched pass runs on: each pair of sibling leaves of a
+    # numerical split is one path (built here, at set-up)
+    t0 = time.time()
+    binfos = [e.batch_info() for e in ens]
+    log(f"prepared the batched pass's pair tables in {time.time() - t0:.1f}s")
     X = [torch.from_numpy(w.X).to(dev) for w in works]
     G = [torch.from_numpy(w.grad_phi).to(dev) for w in works]
 
@@ -218,8 +223,12 @@ def run_ours(args, rank, world, local):
              for e, x, g, p, a, b in zip(ens, X, G, phi, dl, dz)]
     reqs = qts.make_requests(items)
     U = units(works)
-    elem_nodes = sum(w.M * info["sum_unique"] for w, info in zip(works, infos)) * N_QUAD
+    # algorithmic work of the pass as run: per (sample, element of a path of the
+    # pair tables, node) 11 FP32-pipe operations
+    elem_nodes = sum(w.M * b["sum_unique"] for w, b in zip(works, binfos)) * N_QUAD
     alg_ops = elem_nodes * OPS_FUSED
+    # the same computation counted on the per-leaf paths (both leaves of a pair)
+    leaf_ops = sum(w.M * i["sum_unique"] for w, i in zip(works, infos)) * N_QUAD * OPS_FUSED
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
 
@@ -340,7 +349,9 @@ def run_ours(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "requests": len(works), "sample_trees_per_step": U,
-                       "paths": int(sum(i["n_paths"] for i in infos)),
+                       "paths": int(sum(b["n_paths"] for b in binfos)),
+                       "leaf_paths": int(sum(i["n_paths"] for i in infos)),
+                       "pair_paths": int(sum(b["n_pair_paths"] for b in binfos)),
                        "n_quad": N_QUAD, "l2": "flushed between steps (256 MB write)",
                        "accumulation": "f64 across path chunks", "parallelism": "replicas" if world > 1 else "single",
                        "autotune": {"seconds": round(tune_s, 1), "samples_per_request": args.tune_samples,
@@ -353,7 +364,11 @@ def run_ours(args, rank, world, local):
                          "traffic": TRAFFIC_BYTES if kernel_hash() == TRAFFIC_HASH else None,
                          "traffic_unit": "DRAM bytes per step (the persistent launches), scaled from a one-request capture",
                          "peak_basis": f"{sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (max SM clock)",
-                         "algorithmic_ops_per_launch": alg_ops, "kernel_ms": kms,
+                         "algorithmic_ops_per_launch": alg_ops,
+                         "ops_basis": "11 FP32-pipe ops per (sample, path element, node) of the pass's tables, "
+                                      "where each pair of sibling leaves is one path",
+                         "leaf_path_equivalent_tops": leaf_ops / (kms / 1e3) / 1e12,
+                         "kernel_ms": kms,
                          "kernel_ms_source": kms_src},
             "plain_fused": arm(fused_ms, "per request: the same fused forward + adjoint pass, one graph launch each"),
             "plain": arm(plain_ms, "per request: forward launches + adjoint launches + epilogue"),
@@ -470,7 +485,7 @@ def fixed_workloads(qts, dev, stream, flush, reps=5):
         t0 = time.time()
         w = synth.workload(name)
         E = qts.Ensemble.from_arrays(w.ens)
-        info = E.info()
+        info = E.batch_info()  # the FP32 forward runs on the pair tables
         Xd = torch.from_numpy(w.X).to(dev)
         if kind == "phi":
             res = torch.empty((w.M, w.F + 1), dtype=torch.float64, device=dev)
@@ -481,7 +496,7 @@ def fixed_workloads(qts, dev, stream, flush, reps=5):
         ts = time_arm(fn, reps if name != "deep-depth20" else 3, 1, stream, flush)
         E.sync_status()
         t = float(np.median(ts))
-        rec = {"what": kind, "trees": w.ens.n_trees, "M": w.M, "F": w.F, "paths": info["n_paths"],
+        rec = {"what": kind, "trees": w.ens.n_trees, "M": w.M, "F": w.F, "paths": E.info()["n_paths"],
                "ms": t, "sample_trees_per_s": w.M * w.ens.n_trees / (t / 1e3)}
         if kind == "phi":
             ops = OPS_FWD * N_QUAD * info["sum_unique"] * w.M

@@ -307,6 +307,20 @@ qts_status qts_batched_fwd_bwd(int32_t n_requests, const qts_request *reqs, int3
 qts_status qts_batched_autotune(int32_t n_requests, const qts_request *reqs, int32_t n_quad,
                                 int64_t max_samples, int32_t *chosen, qts_stream_t stream);
 
+/*
+ * qts_get_batch_info - size of the path tables the batched pass uses for this
+ * ensemble (built on first use, as by a batched call).  These tables hold each
+ * pair of sibling leaves of a numerical split as one path: the pair's combined
+ * leaf polynomial val_A a_A(p) + val_B a_B(p) is linear in p, so it is one more
+ * element of the shared path (exact algebra of Eq. shap_as_weighted_banzhafs;
+ * the paper evaluates the two paths separately).
+ *   n_paths       paths, pairs counted once
+ *   sum_unique    sum over paths of their unique features (the work unit)
+ *   n_pair_paths  paths that stand for two leaves
+ * Any output pointer may be NULL.
+ */
+qts_status qts_get_batch_info(qts_ensemble *ens, int64_t *n_paths, int64_t *sum_unique, int64_t *n_pair_paths);
+
 /* Number of kernels in the graph of the calling thread's last batched call. */
 int32_t qts_batched_kernel_count(void);
 
@@ -346,8 +360,11 @@ qts_status qts_get_info(const qts_ensemble *ens, qts_info *out);
  * qts_describe_ensemble - host-only dry run of qts_load_ensemble's path
  * preparation (Sec. 2 merging and bucketing): same arguments and checks, no
  * device memory is touched; fills `out` (device_bytes = the bytes an upload
- * would take).  Usable without a GPU.
+ * would take).  Usable without a GPU.  With QTS_DESCRIBE_PAIRS in flags it
+ * describes the tables of the batched pass instead (sibling leaves of a
+ * numerical split as one path; see qts_get_batch_info).
  */
+#define QTS_DESCRIBE_PAIRS 2u
 qts_status qts_describe_ensemble(int32_t n_trees, const int64_t *tree_node_offsets,
                                  const int32_t *left, const int32_t *right, const int32_t *feature,
                                  const float *threshold, const uint8_t *default_left,

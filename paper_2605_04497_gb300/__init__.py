@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libqtreeshap.so")
 
 QTS_OK = 0
 QTS_FLAG_FP64 = 1
+QTS_DESCRIBE_PAIRS = 2
 STATUS_NAMES = {0: "QTS_OK", 1: "QTS_ERR_ARG", 2: "QTS_ERR_CUDA", 3: "QTS_ERR_OOM",
                 4: "QTS_ERR_UNSUPPORTED", 5: "QTS_ERR_TIMEOUT", 6: "QTS_ERR_DEVICE_CHECK"}
 
@@ -25,7 +26,7 @@ STATUS_NAMES = {0: "QTS_OK", 1: "QTS_ERR_ARG", 2: "QTS_ERR_CUDA", 3: "QTS_ERR_OO
 EXPORTS = ("qts_load_ensemble", "qts_load_ensemble_cat", "qts_update_params", "qts_shap_values", "qts_shap_values_alg1",
            "qts_shap_interactions",
            "qts_shap_interactions_noalloc", "qts_shap_interactions3", "qts_shap_interactions_order",
-           "qts_shap_backward", "qts_batched_fwd_bwd", "qts_batched_autotune", "qts_autotune", "qts_sync_status",
+           "qts_shap_backward", "qts_batched_fwd_bwd", "qts_batched_autotune", "qts_get_batch_info", "qts_autotune", "qts_sync_status",
            "qts_get_info", "qts_describe_ensemble", "qts_describe_paths", "qts_describe_alg1_program", "qts_selftest_wait_timeout", "qts_batched_kernel_count", "qts_batched_last_kernel_ms", "qts_gauss_legendre", "qts_last_error",
            "qts_free")
 
@@ -79,6 +80,7 @@ def lib():
         L.qts_shap_backward.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, vp]
         L.qts_batched_fwd_bwd.argtypes = [i32, vp, i32, vp]
         L.qts_batched_autotune.argtypes = [i32, vp, i32, i64, vp, vp]
+        L.qts_get_batch_info.argtypes = [vp, vp, vp, vp]
         L.qts_autotune.argtypes = [vp, vp, i64, i32, ctypes.c_char_p, vp]
         L.qts_sync_status.argtypes = [vp, vp]
         L.qts_selftest_wait_timeout.argtypes = [vp, vp]
@@ -134,15 +136,17 @@ def _info_dict(i: QtsInfo) -> dict:
                 expected_value=i.expected_value, device_bytes=i.device_bytes, flags=i.flags)
 
 
-def describe(ens, fp64: bool = False) -> dict:
-    """Host-only path preparation summary (no GPU needed)."""
+def describe(ens, fp64: bool = False, pairs: bool = False) -> dict:
+    """Host-only path preparation summary (no GPU needed); pairs: the tables of
+    the batched pass (sibling leaves merged)."""
     arr = lambda a, dt: np.ascontiguousarray(a, dtype=dt)
     a = [arr(ens.node_offsets, np.int64), arr(ens.left, np.int32), arr(ens.right, np.int32),
          arr(ens.feature, np.int32), arr(ens.threshold, np.float32), arr(ens.default_left, np.uint8),
          arr(ens.z, np.float32), arr(ens.leaf_value, np.float32)]
     i = QtsInfo()
+    flags = (QTS_FLAG_FP64 if fp64 else 0) | (QTS_DESCRIBE_PAIRS if pairs else 0)
     _check(lib().qts_describe_ensemble(len(a[0]) - 1, *[x.ctypes.data for x in a], int(ens.n_features),
-                                       QTS_FLAG_FP64 if fp64 else 0, ctypes.byref(i)))
+                                       flags, ctypes.byref(i)))
     return _info_dict(i)
 
 
@@ -233,6 +237,12 @@ class Ensemble:
         i = QtsInfo()
         _check(lib().qts_get_info(self.handle, ctypes.byref(i)))
         return _info_dict(i)
+
+    def batch_info(self) -> dict:
+        """Sizes of the tables the batched pass uses (sibling leaf pairs merged)."""
+        n, su, npair = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().qts_get_batch_info(self.handle, ctypes.byref(n), ctypes.byref(su), ctypes.byref(npair)))
+        return dict(n_paths=n.value, sum_unique=su.value, n_pair_paths=npair.value)
 
     def sync_status(self, stream=None):
         _check(lib().qts_sync_status(self.handle, _stream(stream)))

@@ -66,6 +66,18 @@ void release_device(qts_ensemble* e) {
     e->d_empty_leaf = nullptr;
     e->device_bytes = 0;
     release_dfs(e);
+    release_batch_tables(e);
+}
+
+void release_batch_tables(qts_ensemble* e) {
+    DevTables& T = e->bdev;
+    for (void* p : {T.rec, (void*)T.path_leaf, (void*)T.path_zprod, (void*)T.path_val, (void*)T.slot_zexcl,
+                    (void*)T.slot_edge_begin, (void*)T.edge_node, (void*)T.edge_coef, (void*)T.empty_leaf,
+                    (void*)T.pair_leaf2, (void*)T.pair_zprod2, (void*)T.pair_z, (void*)T.pair_gslot})
+        cudaFree(p);
+    T = DevTables();
+    e->bprep = Prepared();
+    e->bready = false;
 }
 
 template <typename T>
@@ -111,6 +123,47 @@ qts_status upload(qts_ensemble* e) {
     std::vector<int64_t>().swap(Pm.slot_edge_begin);
     std::vector<int64_t>().swap(Pm.edge_node);
     std::vector<double>().swap(Pm.edge_coef);
+    return QTS_OK;
+}
+
+// Pair tables of the batched pass: prepared from the host copy of the model
+// with sibling leaves merged, uploaded, host copies dropped.
+qts_status ensure_batch_tables(qts_ensemble* e) {
+    if (e->bready) return QTS_OK;
+    Prepared& P = e->bprep;
+    std::string err;
+    const bool cat = !e->is_cat.empty();
+    qts_status st = prepare(e->n_trees, e->off.data(), e->left.data(), e->right.data(), e->feature.data(),
+                            e->thr.data(), e->defl.data(), e->z.data(), e->leaf.data(),
+                            cat ? e->is_cat.data() : nullptr, cat ? e->cat_left.data() : nullptr,
+                            e->n_features, false, &P, &err, true);
+    if (st != QTS_OK) return fail(st, err);
+    DevTables& T = e->bdev;
+    int64_t tot = 0;
+    st = up((Rec32**)&T.rec, P.rec32, &tot, "upload pair tables");
+    if (st == QTS_OK) st = up(&T.path_leaf, P.path_leaf, &tot, "upload pair tables");
+    if (st == QTS_OK) st = up(&T.path_zprod, P.path_zprod, &tot, "upload pair tables");
+    if (st == QTS_OK) st = up(&T.path_val, P.path_val, &tot, "upload pair tables");
+    if (st == QTS_OK) st = up(&T.slot_zexcl, P.slot_zexcl, &tot, "upload pair tables");
+    if (st == QTS_OK) st = up(&T.slot_edge_begin, P.slot_edge_begin, &tot, "upload pair tables");
+    if (st == QTS_OK) st = up(&T.edge_node, P.edge_node, &tot, "upload pair tables");
+    if (st == QTS_OK) st = up(&T.edge_coef, P.edge_coef, &tot, "upload pair tables");
+    if (st == QTS_OK) st = up(&T.empty_leaf, P.empty_leaf, &tot, "upload pair tables");
+    if (st == QTS_OK) st = up(&T.pair_leaf2, P.pair_leaf2, &tot, "upload pair tables");
+    if (st == QTS_OK) st = up(&T.pair_zprod2, P.pair_zprod2, &tot, "upload pair tables");
+    if (st == QTS_OK) st = up(&T.pair_z, P.pair_z, &tot, "upload pair tables");
+    if (st == QTS_OK) st = up(&T.pair_gslot, P.pair_gslot, &tot, "upload pair tables");
+    if (st != QTS_OK) {
+        release_batch_tables(e);
+        return st;
+    }
+    T.bytes = tot;
+    for (auto* v : {&P.path_zprod, &P.path_val, &P.slot_zexcl, &P.edge_coef, &P.pair_zprod2, &P.pair_z})
+        std::vector<double>().swap(*v);
+    for (auto* v : {&P.path_leaf, &P.slot_edge_begin, &P.edge_node, &P.pair_leaf2, &P.pair_gslot})
+        std::vector<int64_t>().swap(*v);
+    std::vector<Rec32>().swap(P.rec32);
+    e->bready = true;
     return QTS_OK;
 }
 
@@ -292,9 +345,16 @@ qts_status qts_shap_values(qts_ensemble* e, const float* X, int64_t M, int32_t F
     QuadF qf;
     QuadD qd;
     if (!make_quad(n_quad, &qf, &qd)) return fail(QTS_ERR_ARG, "quadrature rule");
-    cudaError_t ce = launch_phi_init(phi, M, F, e->prep.bias, s);
+    // FP32 runs on the pair tables (built on the first call that needs them)
+    const bool fp64 = (e->flags & QTS_FLAG_FP64) != 0;
+    if (!fp64) {
+        st = ensure_batch_tables(e);
+        if (st != QTS_OK) return st;
+    }
+    const Prepared& P = fp64 ? e->prep : e->bprep;
+    cudaError_t ce = launch_phi_init(phi, M, F, P.bias, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "phi init launch");
-    for (const Bucket& b : e->prep.buckets) {
+    for (const Bucket& b : P.buckets) {
         ce = launch_fwd_bucket(e, b, X, M, F, qf, qd, phi, e->tune[b.D], s);
         if (ce != cudaSuccess) return cuda_fail(ce, "forward kernel launch");
     }
@@ -359,9 +419,10 @@ qts_status qts_describe_ensemble(int32_t n_trees, const int64_t* off, const int3
     Prepared P;
     std::string err;
     const bool fp64 = (flags & QTS_FLAG_FP64) != 0;
+    const bool pairs = (flags & QTS_DESCRIBE_PAIRS) != 0;
     qts_status st = prepare(n_trees, off, left, right, feature, threshold,
                             default_left ? default_left : defl.data(), z, leaf_value, nullptr, nullptr,
-                            n_features, fp64, &P, &err);
+                            n_features, fp64, &P, &err, pairs);
     if (st != QTS_OK) return fail(st, err);
     std::memset(out, 0, sizeof(*out));
     out->n_trees = n_trees;

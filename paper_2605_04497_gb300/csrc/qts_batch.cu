@@ -127,9 +127,9 @@ __device__ __forceinline__ bool batch_item(const SegDev& sg, const ReqDev& rq, i
                 sg.rec, p0, p1, sub, st0, st1, bars, s_phase, s_flag, rq.status,
                 [&](int64_t p, const Rec32* r) {
                     double* gsl = sg.g_slot + p * D;
-                    double* gv = sg.g_val + p;
-                    if (has_nan) bwd_path_f32_sp<D, true>(r, xr, gr, my, zs, lane, q, gsl, gv);
-                    else bwd_path_f32_sp<D, false>(r, xr, gr, my, zs, lane, q, gsl, gv);
+                    double* gv = sg.g_val + 2 * p;
+                    if (has_nan) bwd_path_f32_sp<D, true, true>(r, xr, gr, my, zs, lane, q, gsl, gv);
+                    else bwd_path_f32_sp<D, false, true>(r, xr, gr, my, zs, lane, q, gsl, gv);
                 },
                 split);
             if (!ok) return false;
@@ -180,21 +180,21 @@ __device__ __forceinline__ bool batch_item(const SegDev& sg, const ReqDev& rq, i
         [&](int64_t p, const Rec32* r) {
             if (grad) {
                 double* gsl = sg.g_slot + p * D;
-                double* gv = sg.g_val + p;
+                double* gv = sg.g_val + 2 * p;
                 if (priv) {
-                    if (has_nan) bwd_path_f32_pk<D, true, kPhiPrivate>(r, xr, gr, my, lane, q, gsl, gv);
-                    else bwd_path_f32_pk<D, false, kPhiPrivate>(r, xr, gr, my, lane, q, gsl, gv);
+                    if (has_nan) bwd_path_f32_pk<D, true, kPhiPrivate, GlobalCols, GlobalCols, true>(r, xr, gr, my, lane, q, gsl, gv);
+                    else bwd_path_f32_pk<D, false, kPhiPrivate, GlobalCols, GlobalCols, true>(r, xr, gr, my, lane, q, gsl, gv);
                 } else {
-                    if (has_nan) bwd_path_f32_pk<D, true, kPhiAtomic>(r, xr, gr, my, lane, q, gsl, gv);
-                    else bwd_path_f32_pk<D, false, kPhiAtomic>(r, xr, gr, my, lane, q, gsl, gv);
+                    if (has_nan) bwd_path_f32_pk<D, true, kPhiAtomic, GlobalCols, GlobalCols, true>(r, xr, gr, my, lane, q, gsl, gv);
+                    else bwd_path_f32_pk<D, false, kPhiAtomic, GlobalCols, GlobalCols, true>(r, xr, gr, my, lane, q, gsl, gv);
                 }
             } else {
                 if (priv) {
-                    if (has_nan) fwd_path_f32<D, FWD_NP, true, GlobalCols, kPhiPrivate>(r, xr, my, lane, q);
-                    else fwd_path_f32<D, FWD_NP, false, GlobalCols, kPhiPrivate>(r, xr, my, lane, q);
+                    if (has_nan) fwd_path_f32<D, FWD_NP, true, GlobalCols, kPhiPrivate, true>(r, xr, my, lane, q);
+                    else fwd_path_f32<D, FWD_NP, false, GlobalCols, kPhiPrivate, true>(r, xr, my, lane, q);
                 } else {
-                    if (has_nan) fwd_path_f32<D, FWD_NP, true, GlobalCols, kPhiAtomic>(r, xr, my, lane, q);
-                    else fwd_path_f32<D, FWD_NP, false, GlobalCols, kPhiAtomic>(r, xr, my, lane, q);
+                    if (has_nan) fwd_path_f32<D, FWD_NP, true, GlobalCols, kPhiAtomic, true>(r, xr, my, lane, q);
+                    else fwd_path_f32<D, FWD_NP, false, GlobalCols, kPhiAtomic, true>(r, xr, my, lane, q);
                 }
             }
         },
@@ -457,7 +457,8 @@ static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 static BatchWork batch_work(const qts_ensemble* e, int64_t M, int F, bool grad) {
     BatchWork w;
     w.Mpad = (M + 64 * kBatchWarps - 1) / (64 * kBatchWarps) * (64 * kBatchWarps);
-    w.grad_bytes = grad ? align256(sizeof(double) * (size_t)(4 + e->prep.n_paths + e->prep.n_slots)) : 0;
+    // adjoint sums of the pair tables: two per path (a sibling pair's two leaves), one per slot
+    w.grad_bytes = grad ? align256(sizeof(double) * (size_t)(4 + 2 * e->bprep.n_paths + e->bprep.n_slots)) : 0;
     const size_t tbytes = align256(sizeof(float) * (size_t)(F + 1) * (size_t)w.Mpad);
     w.xt_off = w.grad_bytes;
     w.gt_off = w.xt_off + tbytes;
@@ -508,8 +509,8 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
                  R.M, bw.Mpad, R.F, 0, (const int*)(wbase + bw.flag_off), e->d_status};
         if (R.M <= 0) continue;
         double* g_val = grad ? (double*)e->d_work + 4 : nullptr;
-        double* g_slot = grad ? g_val + e->prep.n_paths : nullptr;
-        for (const Bucket& b : e->prep.buckets) {
+        double* g_slot = grad ? g_val + 2 * e->bprep.n_paths : nullptr;
+        for (const Bucket& b : e->bprep.buckets) {
             if (ov && ov->only_width > 0 && b.D != ov->only_width) continue;
             const int cls = batch_class(b.D), ci = class_index(cls);
             const Tune& tn = e->tune[b.D];
@@ -523,8 +524,8 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
             const int per_item = item_samples(mode);
             const int n_tiles = (int)((R.M + per_item - 1) / per_item);
             SegHost s;
-            s.d.rec = (const Rec32*)e->d_rec + b.rec_off;
-            s.d.g_val = grad ? g_val + b.path_base : nullptr;
+            s.d.rec = (const Rec32*)e->bdev.rec + b.rec_off;
+            s.d.g_val = grad ? g_val + 2 * b.path_base : nullptr;
             s.d.g_slot = grad ? g_slot + b.slot_base : nullptr;
             s.d.n_paths = b.n_paths;
             s.d.D = b.D;
@@ -587,14 +588,14 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
         const BatchWork bw = batch_work(R.ens, R.M, R.F, grad);
         char* wbase = (char*)R.ens->d_work;
         if (R.phi && R.M > 0) {
-            err = launch_phi_init(R.phi, R.M, R.F, R.ens->prep.bias, cap);
+            err = launch_phi_init(R.phi, R.M, R.F, R.ens->bprep.bias, cap);
             ++kernels;
         }
         if (grad && err == cudaSuccess) err = cudaMemsetAsync(wbase, 0, bw.grad_bytes, cap);
         // the NaN flag starts set for ensembles with categorical elements, so
         // their items take the NaN-aware (categorical-aware) variant
         if (err == cudaSuccess)
-            err = cudaMemsetAsync(wbase + bw.flag_off, R.ens->prep.has_cat ? 1 : 0, 256, cap);
+            err = cudaMemsetAsync(wbase + bw.flag_off, R.ens->bprep.has_cat ? 1 : 0, 256, cap);
         if (R.M > 0 && err == cudaSuccess) {
             err = launch_transpose(R.X, R.M, R.F, R.F, (float*)(wbase + bw.xt_off), R.F + 1, bw.Mpad,
                                    (int*)(wbase + bw.flag_off), cap);
@@ -637,11 +638,11 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
         if (!R.grad_phi) continue;
         double* gb = (double*)R.ens->d_work;
         double* g_val = gb + 4;
-        double* g_slot = g_val + R.ens->prep.n_paths;
+        double* g_slot = g_val + 2 * R.ens->bprep.n_paths;
         if (R.M > 0) {
-            err = launch_bwd_epilogue(R.ens, R.grad_phi, R.M, R.F, g_val, g_slot, R.d_leaf, R.d_z, gb, cap);
-            kernels += 1 + (R.ens->prep.n_paths + (int64_t)R.ens->prep.empty_leaf.size() > 0) +
-                       (R.ens->prep.n_slots > 0);
+            err = launch_bwd_epilogue_pairs(R.ens, R.grad_phi, R.M, R.F, g_val, g_slot, R.d_leaf, R.d_z, gb, cap);
+            kernels += 1 + (R.ens->bprep.n_paths + (int64_t)R.ens->bprep.empty_leaf.size() > 0) +
+                       (R.ens->bprep.n_slots > 0);
         } else {
             err = cudaMemsetAsync(R.d_leaf, 0, sizeof(double) * R.ens->n_nodes, cap);
             if (err == cudaSuccess) err = cudaMemsetAsync(R.d_z, 0, sizeof(double) * R.ens->n_nodes, cap);
@@ -689,7 +690,9 @@ static qts_status check_batch(int32_t n, const qts_request* reqs, int32_t n_quad
     }
     for (int r = 0; r < n; ++r) {
         const qts_request& R = reqs[r];
-        qts_status st = ensure_workspace(R.ens, batch_work(R.ens, R.M, R.F, R.grad_phi != nullptr).total);
+        qts_status st = ensure_batch_tables(R.ens);
+        if (st != QTS_OK) return st;
+        st = ensure_workspace(R.ens, batch_work(R.ens, R.M, R.F, R.grad_phi != nullptr).total);
         if (st != QTS_OK) return st;
     }
     return QTS_OK;
@@ -711,7 +714,7 @@ extern "C" qts_status qts_batched_fwd_bwd(int32_t n, const qts_request* reqs, in
         for (uint64_t v : {(uint64_t)(uintptr_t)R.ens, (uint64_t)(uintptr_t)R.X, (uint64_t)R.M, (uint64_t)R.F,
                            (uint64_t)(uintptr_t)R.grad_phi, (uint64_t)(uintptr_t)R.phi,
                            (uint64_t)(uintptr_t)R.d_leaf, (uint64_t)(uintptr_t)R.d_z,
-                           (uint64_t)(uintptr_t)R.ens->d_work, (uint64_t)(uintptr_t)R.ens->d_rec,
+                           (uint64_t)(uintptr_t)R.ens->d_work, (uint64_t)(uintptr_t)R.ens->bdev.rec,
                            (uint64_t)R.ens->tune_gen})
             key.push_back(v);
     }
@@ -795,7 +798,7 @@ extern "C" qts_status qts_batched_autotune(int32_t n, const qts_request* reqs, i
     std::vector<char> fused(kMaxD + 1, 0);
     for (const auto& R : sub) {
         if (R.M <= 0) continue;
-        for (const Bucket& b : R.ens->prep.buckets) {
+        for (const Bucket& b : R.ens->bprep.buckets) {
             if (b.n_paths == 0) continue;
             work[b.D] += (double)R.M * (double)b.n_paths * b.D;
             if (R.grad_phi) fused[b.D] = 1;
@@ -853,6 +856,18 @@ extern "C" qts_status qts_batched_autotune(int32_t n, const qts_request* reqs, i
             chosen[2 * D] = best_paths[D];
             chosen[2 * D + 1] = best_mode[D];
         }
+    return QTS_OK;
+}
+
+extern "C" qts_status qts_get_batch_info(qts_ensemble* e, int64_t* n_paths, int64_t* sum_unique,
+                                         int64_t* n_pair_paths) {
+    if (!e) return fail(QTS_ERR_ARG, "ensemble handle is NULL");
+    if (e->flags & QTS_FLAG_FP64) return fail(QTS_ERR_UNSUPPORTED, "batched calls use FP32 tables");
+    const qts_status st = ensure_batch_tables(e);
+    if (st != QTS_OK) return st;
+    if (n_paths) *n_paths = e->bprep.n_paths;
+    if (sum_unique) *sum_unique = e->bprep.sum_unique;
+    if (n_pair_paths) *n_pair_paths = e->bprep.n_pair_paths;
     return QTS_OK;
 }
 

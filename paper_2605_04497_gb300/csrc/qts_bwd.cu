@@ -306,6 +306,70 @@ cudaError_t launch_bwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
     }
 }
 
+// Pair tables: d_leaf of each path's leaf, and of leaf B of a sibling pair.
+// The kernel leaves sum_s o_A K and sum_s o_B K in g_val[2p], g_val[2p + 1]
+// (o K = the leaf's share of the pair element's adjoint); dL/dval_k adds
+// z_k * Q with Q the pair element's slot sum, and the bias term G prod z.
+__global__ void pair_path_epilogue_kernel(int64_t n_paths, const int64_t* __restrict__ leaf,
+                                          const double* __restrict__ zprod, const int64_t* __restrict__ leaf2,
+                                          const double* __restrict__ zprod2, const double* __restrict__ pz,
+                                          const int64_t* __restrict__ gslot, const double* __restrict__ g_val,
+                                          const double* __restrict__ g_slot, const double* __restrict__ gb,
+                                          int64_t n_empty, const int64_t* __restrict__ empty_leaf, double* d_leaf) {
+    const double G = *gb;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_paths + n_empty;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        if (p >= n_paths) {
+            d_leaf[empty_leaf[p - n_paths]] = G;
+            continue;
+        }
+        const int64_t l2 = leaf2[p];
+        if (l2 < 0) {
+            d_leaf[leaf[p]] = g_val[2 * p] + G * zprod[p];
+        } else {
+            const double Q = g_slot[gslot[p]];
+            d_leaf[leaf[p]] = pz[2 * p] * Q + g_val[2 * p] + G * zprod[p];
+            d_leaf[l2] = pz[2 * p + 1] * Q + g_val[2 * p + 1] + G * zprod2[p];
+        }
+    }
+}
+
+static SlotMap slot_map(const Prepared& P) {
+    SlotMap sm;
+    sm.nb = (int)P.buckets.size();
+    for (int b = 0; b < sm.nb; ++b) {
+        sm.slot_base[b] = P.buckets[b].slot_base;
+        sm.path_base[b] = P.buckets[b].path_base;
+        sm.D[b] = P.buckets[b].D;
+    }
+    sm.slot_base[sm.nb] = P.n_slots;
+    return sm;
+}
+
+cudaError_t launch_bwd_epilogue_pairs(const qts_ensemble* e, const float* grad, int64_t M, int F,
+                                      const double* g_val, const double* g_slot, double* d_leaf,
+                                      double* d_z, double* gb, cudaStream_t st) {
+    const Prepared& P = e->bprep;
+    const DevTables& T = e->bdev;
+    cudaError_t err = cudaMemsetAsync(d_leaf, 0, sizeof(double) * e->n_nodes, st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(d_z, 0, sizeof(double) * e->n_nodes, st);
+    if (err != cudaSuccess) return err;
+    bias_grad_kernel<<<1, 1024, 0, st>>>(grad, M, F, gb);
+    const int64_t np = P.n_paths + (int64_t)P.empty_leaf.size();
+    if (np > 0) {
+        const int blocks = (int)std::min<int64_t>((np + 255) / 256, 8 * 152);
+        pair_path_epilogue_kernel<<<blocks, 256, 0, st>>>(P.n_paths, T.path_leaf, T.path_zprod, T.pair_leaf2,
+                                                          T.pair_zprod2, T.pair_z, T.pair_gslot, g_val, g_slot, gb,
+                                                          (int64_t)P.empty_leaf.size(), T.empty_leaf, d_leaf);
+    }
+    if (P.n_slots > 0) {
+        const int blocks = (int)std::min<int64_t>((P.n_slots + 255) / 256, 8 * 152);
+        slot_epilogue_kernel<<<blocks, 256, 0, st>>>(slot_map(P), g_slot, T.path_val, T.slot_zexcl,
+                                                     T.slot_edge_begin, T.edge_node, T.edge_coef, gb, d_z);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bwd_epilogue(const qts_ensemble* e, const float* grad, int64_t M, int F,
                                 const double* g_val, const double* g_slot, double* d_leaf,
                                 double* d_z, double* gb, cudaStream_t st) {

@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
             if constexpr (!FP64) {
                 if (!valid) return;
                 const SmemCols xr{xs, col};
-                if (has_nan) fwd_path_f32<D, NP, true, SmemCols, kPhiAtomic>(r, xr, ps, col, a.q);
-                else fwd_path_f32<D, NP, false, SmemCols, kPhiAtomic>(r, xr, ps, col, a.q);
+                if (has_nan) fwd_path_f32<D, NP, true, SmemCols, kPhiAtomic, true>(r, xr, ps, col, a.q);
+                else fwd_path_f32<D, NP, false, SmemCols, kPhiAtomic, true>(r, xr, ps, col, a.q);
             }
         });
         ok = true;
@@ -142,11 +142,11 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
             } else {
                 const SmemCols xr{my_xs, lane};
                 if (priv) {
-                    if (has_nan) fwd_path_f32<D, NP, true, SmemCols, kPhiPrivate>(r, xr, my_ps, lane, a.q);
-                    else fwd_path_f32<D, NP, false, SmemCols, kPhiPrivate>(r, xr, my_ps, lane, a.q);
+                    if (has_nan) fwd_path_f32<D, NP, true, SmemCols, kPhiPrivate, true>(r, xr, my_ps, lane, a.q);
+                    else fwd_path_f32<D, NP, false, SmemCols, kPhiPrivate, true>(r, xr, my_ps, lane, a.q);
                 } else {
-                    if (has_nan) fwd_path_f32<D, NP, true, SmemCols, kPhiAtomic>(r, xr, my_ps, lane, a.q);
-                    else fwd_path_f32<D, NP, false, SmemCols, kPhiAtomic>(r, xr, my_ps, lane, a.q);
+                    if (has_nan) fwd_path_f32<D, NP, true, SmemCols, kPhiAtomic, true>(r, xr, my_ps, lane, a.q);
+                    else fwd_path_f32<D, NP, false, SmemCols, kPhiAtomic, true>(r, xr, my_ps, lane, a.q);
                 }
             }
         },
@@ -261,8 +261,9 @@ cudaError_t launch_fwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
     if (M <= 0 || b.n_paths == 0) return cudaSuccess;
     const bool fp64 = (e->flags & QTS_FLAG_FP64) != 0;
     FwdArgs a;
+    // FP32: the pair tables (sibling leaves merged), whose buckets the caller walks
     a.rec = fp64 ? (const void*)((const Rec64*)e->d_rec + b.rec_off)
-                 : (const void*)((const Rec32*)e->d_rec + b.rec_off);
+                 : (const void*)((const Rec32*)e->bdev.rec + b.rec_off);
     a.n_paths = b.n_paths;
     a.sub = std::max(1, tn.sub);
     const int warps = std::max(1, std::min(8, tn.warps));
@@ -285,7 +286,7 @@ cudaError_t launch_fwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
     a.X = X;
     a.M = M;
     a.F = F;
-    a.cat = e->prep.has_cat ? 1 : 0;
+    a.cat = (fp64 ? e->prep.has_cat : e->bprep.has_cat) ? 1 : 0;
     a.phi = phi;
     a.status = e->d_status;
     a.q = q;

@@ -46,6 +46,15 @@ constexpr uint32_t kNanOk = 0x80000000u;
 constexpr uint32_t kCat = 0x40000000u;
 constexpr uint32_t kOtherOk = 0x20000000u;
 constexpr uint32_t kFeatMask = 0x00FFFFFFu;
+// Sibling-pair element (pair tables of the batched pass; always the path's last
+// record).  Leaves A (left) and B (right) of a numerical split at threshold
+// theta share every other element; this one has z = alpha = val_A z_A +
+// val_B z_B and [lo, hi) = the interval of the splits on the feature above the
+// pair, and a sample x gives d = (x in [lo, hi) ? (x < theta ? dA : dB) : -alpha)
+// (NaN: kNanOk and kDefLeft choose).  The path header holds {1 (val), dA =
+// val_A - alpha, dB = val_B - alpha, bits of theta}.
+constexpr uint32_t kPairElem = 0x10000000u;
+constexpr uint32_t kDefLeft = 0x08000000u;
 
 // FP64 table: 32-byte records {z, 0, lo, hi, bits, 0}; header {val, prod z}.
 struct __align__(16) Rec64 {
@@ -88,6 +97,13 @@ struct Prepared {
     int max_unique = 0;
     double bias = 0.0;  // E[f]
     bool has_cat = false;  // some element is categorical: kernels take their NaN-aware variant
+    // pair tables (sibling leaves of a numerical split as one path, kPairElem)
+    bool pairs = false;
+    int64_t n_pair_paths = 0;
+    std::vector<int64_t> pair_leaf2;   // per path: leaf B of a pair, -1 otherwise (path_leaf is A)
+    std::vector<double> pair_zprod2;   // per path: prod of leaf B's merged z (path_zprod is A's)
+    std::vector<double> pair_z;        // per path: z_A, z_B of the pair element
+    std::vector<int64_t> pair_gslot;   // per path: slot of the pair element, -1 otherwise
 };
 
 // Prepare the path tables (host, multi-threaded).  Returns QTS_OK or an error
@@ -95,10 +111,28 @@ struct Prepared {
 qts_status prepare(int32_t n_trees, const int64_t* off, const int32_t* left, const int32_t* right,
                    const int32_t* feature, const float* thr, const uint8_t* defl, const float* z,
                    const float* leaf, const uint8_t* is_cat, const uint64_t* cat_left, int32_t F,
-                   bool fp64, Prepared* out, std::string* err);
+                   bool fp64, Prepared* out, std::string* err, bool pairs = false);
 
 // Gauss-Legendre nodes on [0,1] (Golub-Welsch via Jacobi eigen-decomposition).
 bool gauss_legendre(int n, double* t, double* w);
+
+// Device copies of one set of path tables and the adjoint's metadata.
+struct DevTables {
+    void* rec = nullptr;               // Rec32 records
+    int64_t* path_leaf = nullptr;
+    double* path_zprod = nullptr;
+    double* path_val = nullptr;
+    double* slot_zexcl = nullptr;
+    int64_t* slot_edge_begin = nullptr;
+    int64_t* edge_node = nullptr;
+    double* edge_coef = nullptr;
+    int64_t* empty_leaf = nullptr;
+    int64_t* pair_leaf2 = nullptr;     // pair tables only
+    double* pair_zprod2 = nullptr;
+    double* pair_z = nullptr;
+    int64_t* pair_gslot = nullptr;
+    int64_t bytes = 0;
+};
 
 // Launch tuning of one bucket width.
 struct Tune {
@@ -152,6 +186,11 @@ struct qts_ensemble {
     int64_t* d_dfs_off = nullptr;     // per tree, n_trees + 1
     int dfs_levels = 0;               // internal-node depth + 1
     int64_t dfs_records = 0;
+    // pair tables of the batched pass (sibling leaves merged), built on the
+    // first batched call that includes this ensemble
+    qts::Prepared bprep;
+    qts::DevTables bdev;
+    bool bready = false;
     // per-width launch tuning (index = bucket width)
     qts::Tune tune[qts::kMaxD + 1];
     bool tuned = false;
@@ -167,6 +206,8 @@ qts_status ensure_workspace(qts_ensemble* e, size_t bytes);
 qts_status upload(qts_ensemble* e);
 void release_device(qts_ensemble* e);
 void release_dfs(qts_ensemble* e);      // drop the depth-first program (rebuilt on demand)
+qts_status ensure_batch_tables(qts_ensemble* e);  // build the pair tables of the batched pass
+void release_batch_tables(qts_ensemble* e);
 int num_sms();
 void batch_forget(const qts_ensemble* e);  // drop cached batched graphs using e
 
@@ -207,5 +248,9 @@ cudaError_t launch_bwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
 cudaError_t launch_bwd_epilogue(const qts_ensemble* e, const float* grad, int64_t M, int F,
                                 const double* g_val, const double* g_slot, double* d_leaf,
                                 double* d_z, double* g_bias_scratch, cudaStream_t st);
+// the same for the pair tables of the batched pass (two g_val sums per path)
+cudaError_t launch_bwd_epilogue_pairs(const qts_ensemble* e, const float* grad, int64_t M, int F,
+                                      const double* g_val, const double* g_slot, double* d_leaf,
+                                      double* d_z, double* g_bias_scratch, cudaStream_t st);
 
 }  // namespace qts

@@ -30,6 +30,38 @@ struct GlobalCols {  // transposed global copy [feature][ld]; this lane's sample
     __device__ __forceinline__ float operator()(int f) const { return __ldg(t + (int64_t)f * ld + s); }
 };
 
+// ------------------------------------------------------- sibling pairs --
+//
+// Pair tables (batched pass) hold sibling leaves A, B of a numerical split as
+// one path with val = 1 whose last element e (kPairElem) stands for both: for a
+// sample x it gives d = val_k - alpha for the leaf k the sample reaches (x in
+// the element's interval, then left of theta), -alpha if neither.  h is the
+// path header {1, val_A - alpha, val_B - alpha, bits of theta}.
+__device__ __forceinline__ void pair_sides(float x, const Rec32& e, const Rec32& h, bool* oa, bool* ob) {
+    bool in, left;
+    if (x != x) {
+        in = (e.bits & kNanOk) != 0;
+        left = (e.bits & kDefLeft) != 0;
+    } else {
+        in = x >= e.lo && x < e.hi;
+        left = x < __uint_as_float(h.bits);
+    }
+    *oa = in && left;
+    *ob = in && !left;
+}
+
+__device__ __forceinline__ float pair_d(float x, const Rec32& e, const Rec32& h) {
+    bool oa, ob;
+    pair_sides(x, e, h, &oa, &ob);
+    return oa ? h.lo : (ob ? h.hi : -e.z);
+}
+
+// The two extra sums of a pair path's adjoint.  With Q = acc2 - g acc1 the
+// pair element's z-gradient at val = 1 and K = acc3 - acc2 + g acc1 (acc3 =
+// sum_m w_m U_m, the part of acc2 without the (1 - t_m) factor), per sample
+// dL/dval_A = z_A Q + o_A K and dL/dval_B = z_B Q + o_B K; the epilogue adds
+// z_k * (sum of Q) from the element's slot, the kernel sums o_A K and o_B K.
+
 // ====================================================== first order ======
 //
 // c_i = sum_m w_m val prod_{j<i} a_j(t_m) prod_{j>i} a_j(t_m), a_j(t) = z_j + t (o_j - z_j),
@@ -38,11 +70,12 @@ struct GlobalCols {  // transposed global copy [feature][ld]; this lane's sample
 // (Thm 1 with S = {i}, Eq. shap_as_weighted_banzhafs).
 
 
-template <int D, int NP, bool HAS_NAN, typename XR, int PHI = kPhiAtomic>
+template <int D, int NP, bool HAS_NAN, typename XR, int PHI = kPhiAtomic, bool PAIRS = false>
 __device__ __forceinline__ void fwd_path_f32(const Rec32* __restrict__ r, const XR& xr, float* ps, int lane,
                                              const QuadF& q) {
     constexpr int K = NP / 2;  // node pairs per pass
     const float val = r[0].z;
+    const bool pair = PAIRS && (r[D].bits & kPairElem) != 0;
     float dd[D], zz[D];
     int ff[D];
 #pragma unroll
@@ -52,6 +85,7 @@ __device__ __forceinline__ void fwd_path_f32(const Rec32* __restrict__ r, const 
         const float x = xr(f);
         const bool o = satisfies<HAS_NAN>(x, e.lo, e.hi, e.bits);
         dd[j] = (o ? 1.f : 0.f) - e.z;
+        if (j == D - 1 && pair) dd[j] = pair_d(x, e, r[0]);
         zz[j] = e.z;
         ff[j] = f;
     }
@@ -310,19 +344,21 @@ __device__ __forceinline__ void bwd_path_f32(const Rec32* __restrict__ r, const 
 // node loop touches kept as register pairs - {d_j, d_j}, {u_j, u_j} and the two
 // per-element accumulators - so a pass issues only the 12 packed operations per
 // element plus the z reload; the pair halves are added once after all passes.
-template <int D, bool HAS_NAN, int PHI, typename XR, typename GR>
+template <int D, bool HAS_NAN, int PHI, typename XR, typename GR, bool PAIRS = false>
 __device__ __forceinline__ void bwd_path_f32_pk(const Rec32* __restrict__ r, const XR& xr, const GR& gr,
                                                 float* ps, int lane, const QuadF& q, double* g_slot_p,
                                                 double* g_val_p) {
     const float val = r[0].z;
-    float2 d2[D], u2[D], a1[D], a2[D];
+    const bool pair = PAIRS && (r[D].bits & kPairElem) != 0;
+    float2 d2[D], u2[D], a1[D], a2[D], a3 = f2s(0.f);
 #pragma unroll
     for (int j = 0; j < D; ++j) {
         const Rec32 e = r[1 + j];
         const int f = feat_of(e.bits);
         const float x = xr(f);
         const bool o = satisfies<HAS_NAN>(x, e.lo, e.hi, e.bits);
-        const float d = (o ? 1.f : 0.f) - e.z;
+        float d = (o ? 1.f : 0.f) - e.z;
+        if (j == D - 1 && pair) d = pair_d(x, e, r[0]);
         d2[j] = f2s(d);
         u2[j] = f2s(gr(f) * d);
         a1[j] = f2s(0.f);
@@ -342,6 +378,7 @@ __device__ __forceinline__ void bwd_path_f32_pk(const Rec32* __restrict__ r, con
             P[j + 1] = mul2(P[j], a);
             PU[j + 1] = fma2(PU[j], a, mul2(u2[j], P[j]));
         }
+        if constexpr (PAIRS && D > 1) a3 = add2(a3, PU[D - 1]);
         float2 S = f2s(1.f), SU = f2s(0.f);
 #pragma unroll
         for (int j = D - 1; j >= 0; --j) {
@@ -362,6 +399,21 @@ __device__ __forceinline__ void bwd_path_f32_pk(const Rec32* __restrict__ r, con
         dval = fmaf(u2[j].x, c1, dval);
         dz[j] = val * (c2 - gr(f) * c1);
         phi_add<PHI>(ps, f * kTileLd + lane, val * d2[j].x * c1);
+    }
+    if constexpr (PAIRS) {
+        if (pair) {  // val = 1: dval becomes o_A K, a second sum o_B K goes to g_val_p[1]
+            const Rec32 e = r[D];
+            const int f = feat_of(e.bits);
+            bool oa, ob;
+            pair_sides(xr(f), e, r[0], &oa, &ob);
+            const float c1 = a1[D - 1].x + a1[D - 1].y, c2 = a2[D - 1].x + a2[D - 1].y;
+            const float k = (a3.x + a3.y) - c2 + gr(f) * c1;
+            dval = oa ? k : 0.f;
+            float rb = ob ? k : 0.f;
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) rb += __shfl_xor_sync(0xffffffffu, rb, off);
+            if (lane == 0) atomicAdd(g_val_p + 1, (double)rb);
+        }
     }
     flush_path_grads<D, float>(dz, dval, lane, g_slot_p, g_val_p);
 }
@@ -393,12 +445,13 @@ struct GlobalCols2 {  // transposed global copy [feature][ld]; samples s, s+1 (s
     }
 };
 
-template <int D, bool HAS_NAN>
+template <int D, bool HAS_NAN, bool PAIRS = false>
 __device__ __forceinline__ void bwd_path_f32_sp(const Rec32* __restrict__ r, const GlobalCols2& xr,
                                                 const GlobalCols2& gr, float* ps, float2* zs, int lane,
                                                 const QuadF& q, double* g_slot_p, double* g_val_p) {
     const float val = r[0].z;
-    float2 d2[D], u2[D], a1[D], a2[D];
+    const bool pair = PAIRS && (r[D].bits & kPairElem) != 0;
+    float2 d2[D], u2[D], a1[D], a2[D], a3 = f2s(0.f);
     __syncwarp();
     if (lane < D) zs[lane] = f2s(r[1 + lane].z);
 #pragma unroll
@@ -409,6 +462,7 @@ __device__ __forceinline__ void bwd_path_f32_sp(const Rec32* __restrict__ r, con
         const bool oa = satisfies<HAS_NAN>(x.x, e.lo, e.hi, e.bits);
         const bool ob = satisfies<HAS_NAN>(x.y, e.lo, e.hi, e.bits);
         d2[j] = f2((oa ? 1.f : 0.f) - e.z, (ob ? 1.f : 0.f) - e.z);
+        if (j == D - 1 && pair) d2[j] = f2(pair_d(x.x, e, r[0]), pair_d(x.y, e, r[0]));
         u2[j] = mul2(gr(f), d2[j]);
         a1[j] = f2s(0.f);
         a2[j] = f2s(0.f);
@@ -426,6 +480,7 @@ __device__ __forceinline__ void bwd_path_f32_sp(const Rec32* __restrict__ r, con
             P[j + 1] = mul2(P[j], a);
             PU[j + 1] = fma2(PU[j], a, mul2(u2[j], P[j]));
         }
+        if constexpr (PAIRS && D > 1) a3 = add2(a3, PU[D - 1]);
         float2 S = f2s(1.f), SU = f2s(0.f);
 #pragma unroll
         for (int j = D - 1; j >= 0; --j) {
@@ -449,6 +504,22 @@ __device__ __forceinline__ void bwd_path_f32_sp(const Rec32* __restrict__ r, con
         dz[j] = dzj.x + dzj.y;
         float2* cell = reinterpret_cast<float2*>(ps + f * kTileLd2 + 2 * lane);
         *cell = fma2(mul2(v2, d2[j]), a1[j], *cell);  // private tile: plain read-add-write
+    }
+    if constexpr (PAIRS) {
+        if (pair) {  // val = 1: dval becomes o_A K, a second sum o_B K goes to g_val_p[1]
+            const Rec32 e = r[D];
+            const int f = feat_of(e.bits);
+            const float2 x = xr(f);
+            bool oa0, ob0, oa1, ob1;
+            pair_sides(x.x, e, r[0], &oa0, &ob0);
+            pair_sides(x.y, e, r[0], &oa1, &ob1);
+            const float2 k = fma2(gr(f), a1[D - 1], fma2(f2s(-1.f), a2[D - 1], a3));
+            dval2 = f2(oa0 ? k.x : 0.f, oa1 ? k.y : 0.f);
+            float rb = (ob0 ? k.x : 0.f) + (ob1 ? k.y : 0.f);
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) rb += __shfl_xor_sync(0xffffffffu, rb, off);
+            if (lane == 0) atomicAdd(g_val_p + 1, (double)rb);
+        }
     }
     flush_path_grads<D, float>(dz, dval2.x + dval2.y, lane, g_slot_p, g_val_p);
 }

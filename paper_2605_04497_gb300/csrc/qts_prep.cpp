@@ -123,11 +123,20 @@ struct ElemTmp {
     int32_t edge_off, edge_cnt;  // into the thread's edge list
 };
 
+// A path of the tables.  A sibling pair (pair tables only) is one path whose
+// last element stands for both leaves A (left) and B (right) of node v: val =
+// 1, the element's z = alpha = val_A z_A + val_B z_B, and a sample's
+// d = val_A o_A + val_B o_B - alpha, where z_k and o_k are leaf k's merged
+// weight and indicator for v's feature (both leaves share every other element).
 struct PathTmp {
     int64_t leaf;
     double val;
     int32_t d;
     int64_t el_off;  // into the thread's element list
+    int64_t leaf2 = -1;  // B (pairs)
+    double val_a = 0, val_b = 0, z_a = 0, z_b = 0, alpha = 0;
+    float theta = 0.f;
+    uint8_t def_left = 0;
 };
 
 struct ThreadOut {
@@ -135,6 +144,7 @@ struct ThreadOut {
     std::vector<ElemTmp> elems;
     std::vector<int64_t> edge_node;
     std::vector<double> edge_w;
+    std::vector<double> edge_cf;  // coefficient fixed at extraction (pair elements), else NaN
     std::vector<int64_t> empty_leaf;
     std::vector<double> empty_val;
     int64_t n_leaves = 0;
@@ -145,7 +155,8 @@ struct ThreadOut {
 
 void extract_trees(int t0, int t1, const int64_t* off, const int32_t* left, const int32_t* right,
                    const int32_t* feature, const float* thr, const uint8_t* defl, const float* z,
-                   const float* leaf, const uint8_t* is_cat, const uint64_t* cat_left, ThreadOut* out) {
+                   const float* leaf, const uint8_t* is_cat, const uint64_t* cat_left, bool pairs,
+                   ThreadOut* out) {
     std::vector<EdgeRec> path;
     struct Item { int32_t v; int32_t depth; EdgeRec in; };
     std::vector<Item> stack;
@@ -182,11 +193,11 @@ void extract_trees(int t0, int t1, const int64_t* off, const int32_t* left, cons
                 path[it.depth - 1] = it.in;
             }
             int64_t g = base + it.v;
-            if (left[g] < 0) {
-                out->n_leaves++;
-                // merge the splits on each feature (Eq. q_def)
+            // merge the splits on each feature of the first `depth` edges (Eq. q_def);
+            // returns the number of elements, or -1 (error set) above kMaxD
+            auto merge = [&](int depth) -> int {
                 int d = 0;
-                for (int k = 0; k < it.depth; ++k) {
+                for (int k = 0; k < depth; ++k) {
                     const EdgeRec& e = path[k];
                     int slot = -1;
                     for (int j = 0; j < d; ++j)
@@ -196,7 +207,7 @@ void extract_trees(int t0, int t1, const int64_t* off, const int32_t* left, cons
                             out->st = QTS_ERR_UNSUPPORTED;
                             out->err = "a path of tree " + std::to_string(t) + " has more than " +
                                        std::to_string(kMaxD) + " unique features";
-                            return;
+                            return -1;
                         }
                         slot = d++;
                         merged[slot] = {e.feat, 1, 0, 1, 1.0, -INFINITY, INFINITY, ~0ull, 0, 0};
@@ -220,10 +231,13 @@ void extract_trees(int t0, int t1, const int64_t* off, const int32_t* left, cons
                     medges[slot].push_back(e.child);
                     mw[slot].push_back(e.w);
                 }
-                // sort elements by feature index (insertion sort on indices)
+                return d;
+            };
+            // emit elements merged[order[0..n)] (sorted by feature) to the thread's lists
+            auto emit_sorted = [&](int n, const int* idx) {
                 int order[kMaxD];
-                for (int j = 0; j < d; ++j) order[j] = j;
-                for (int j = 1; j < d; ++j) {
+                for (int j = 0; j < n; ++j) order[j] = idx[j];
+                for (int j = 1; j < n; ++j) {
                     int key = order[j], k = j - 1;
                     while (k >= 0 && merged[order[k]].feat > merged[key].feat) {
                         order[k + 1] = order[k];
@@ -231,8 +245,7 @@ void extract_trees(int t0, int t1, const int64_t* off, const int32_t* left, cons
                     }
                     order[k + 1] = key;
                 }
-                PathTmp p{g, (double)leaf[g], d, (int64_t)out->elems.size()};
-                for (int jj = 0; jj < d; ++jj) {
+                for (int jj = 0; jj < n; ++jj) {
                     int j = order[jj];
                     ElemTmp m = merged[j];
                     m.edge_off = (int32_t)out->edge_node.size();
@@ -240,11 +253,93 @@ void extract_trees(int t0, int t1, const int64_t* off, const int32_t* left, cons
                     for (size_t a = 0; a < medges[j].size(); ++a) {
                         out->edge_node.push_back(medges[j][a]);
                         out->edge_w.push_back(mw[j][a]);
+                        out->edge_cf.push_back(NAN);
                     }
                     out->elems.push_back(m);
                 }
+            };
+            if (left[g] < 0) {
+                out->n_leaves++;
+                const int d = merge(it.depth);
+                if (d < 0) return;
+                int idx[kMaxD];
+                for (int j = 0; j < d; ++j) idx[j] = j;
+                PathTmp p{g, (double)leaf[g], d, (int64_t)out->elems.size()};
+                emit_sorted(d, idx);
                 out->paths.push_back(p);
                 out->max_unique = std::max(out->max_unique, d);
+                continue;
+            }
+            const int64_t ga = base + left[g], gb = base + right[g];
+            if (pairs && left[ga] < 0 && left[gb] < 0 && !(is_cat && is_cat[g])) {
+                // both children are leaves of a numerical split: one pair path
+                visited += 2;
+                if (visited > nt) {
+                    out->st = QTS_ERR_ARG;
+                    out->err = "tree " + std::to_string(t) + " is not a tree (a node is reached twice)";
+                    return;
+                }
+                out->n_leaves += 2;
+                int d = merge(it.depth);
+                if (d < 0) return;
+                const int32_t f = feature[g];
+                int prev = -1;
+                for (int j = 0; j < d; ++j)
+                    if (merged[j].feat == f) prev = j;
+                if (prev < 0 && d == kMaxD) {
+                    out->st = QTS_ERR_UNSUPPORTED;
+                    out->err = "a path of tree " + std::to_string(t) + " has more than " + std::to_string(kMaxD) +
+                               " unique features";
+                    return;
+                }
+                // the pair element: v's feature merged over the path, then each child
+                ElemTmp m = prev >= 0 ? merged[prev]
+                                      : ElemTmp{f, 1, 0, 1, 1.0, -INFINITY, INFINITY, ~0ull, 0, 0};
+                const double zp = m.z;
+                const double wa = (double)z[ga], wb = (double)z[gb];
+                PathTmp p{ga, 1.0, 0, 0};
+                p.leaf2 = gb;
+                p.val_a = (double)leaf[ga];
+                p.val_b = (double)leaf[gb];
+                p.z_a = zp * wa;
+                p.z_b = zp * wb;
+                p.alpha = p.val_a * p.z_a + p.val_b * p.z_b;
+                p.theta = thr[g];
+                p.def_left = defl ? (defl[g] != 0) : 1;
+                int idx[kMaxD], n = 0;
+                for (int j = 0; j < d; ++j)
+                    if (j != prev) idx[n++] = j;
+                p.el_off = (int64_t)out->elems.size();
+                p.d = n + 1;
+                emit_sorted(n, idx);
+                // its edges: dL/dw_e = sum over the two leaves k of dL/dz_k dz_k/dw_e,
+                // and dL/dz_k = val_k * (the element's z-gradient at val = 1)
+                m.z = p.alpha;
+                m.edge_off = (int32_t)out->edge_node.size();
+                m.edge_cnt = 0;
+                const std::vector<int64_t> no_edges;
+                const std::vector<int64_t>& pe = prev >= 0 ? medges[prev] : no_edges;
+                const std::vector<double> no_w;
+                const std::vector<double>& pw = prev >= 0 ? mw[prev] : no_w;
+                for (int k = 0; k < 2; ++k) {
+                    const double vk = k == 0 ? p.val_a : p.val_b, wk = k == 0 ? wa : wb;
+                    for (size_t a = 0; a < pe.size(); ++a) {
+                        double others = wk;
+                        for (size_t c = 0; c < pe.size(); ++c)
+                            if (c != a) others *= pw[c];
+                        out->edge_node.push_back(pe[a]);
+                        out->edge_w.push_back(pw[a]);
+                        out->edge_cf.push_back(vk * others);
+                        ++m.edge_cnt;
+                    }
+                    out->edge_node.push_back(k == 0 ? ga : gb);
+                    out->edge_w.push_back(wk);
+                    out->edge_cf.push_back(vk * zp);
+                    ++m.edge_cnt;
+                }
+                out->elems.push_back(m);
+                out->paths.push_back(p);
+                out->max_unique = std::max(out->max_unique, p.d);
                 continue;
             }
             int32_t f = feature[g];
@@ -349,7 +444,8 @@ static qts_status validate(int32_t n_trees, const int64_t* off, const int32_t* l
 qts_status prepare(int32_t n_trees, const int64_t* off, const int32_t* left, const int32_t* right,
                    const int32_t* feature, const float* thr, const uint8_t* defl, const float* z,
                    const float* leaf, const uint8_t* is_cat, const uint64_t* cat_left, int32_t F,
-                   bool fp64, Prepared* P, std::string* err) {
+                   bool fp64, Prepared* P, std::string* err, bool pairs) {
+    if (pairs && fp64) { *err = "sibling pairs are built for the FP32 tables only"; return QTS_ERR_ARG; }
     qts_status st = validate(n_trees, off, left, right, feature, thr, z, leaf, is_cat, cat_left, F, err);
     if (st != QTS_OK) return st;
     *P = Prepared();
@@ -371,7 +467,7 @@ qts_status prepare(int32_t n_trees, const int64_t* off, const int32_t* left, con
         std::vector<std::thread> th;
         for (int k = 0; k < nth; ++k)
             th.emplace_back(extract_trees, cut[k], cut[k + 1], off, left, right, feature, thr, defl,
-                            z, leaf, is_cat, cat_left, &outs[k]);
+                            z, leaf, is_cat, cat_left, pairs, &outs[k]);
         for (auto& x : th) x.join();
     }
     for (auto& o : outs)
@@ -415,6 +511,13 @@ qts_status prepare(int32_t n_trees, const int64_t* off, const int32_t* left, con
     P->path_val.resize((size_t)path_total);
     P->slot_edge_begin.assign((size_t)slot_total + 1, 0);
     P->slot_zexcl.assign((size_t)slot_total, 0.0);
+    P->pairs = pairs;
+    if (pairs) {
+        P->pair_leaf2.assign((size_t)path_total, -1);
+        P->pair_zprod2.assign((size_t)path_total, 0.0);
+        P->pair_z.assign(2 * (size_t)path_total, 0.0);
+        P->pair_gslot.assign((size_t)path_total, -1);
+    }
 
     // fill, bucket by bucket in tree order; first count edges per slot
     std::vector<int64_t> cursor(P->buckets.size());
@@ -427,13 +530,28 @@ qts_status prepare(int32_t n_trees, const int64_t* off, const int32_t* left, con
             int64_t lp = cursor[bidx_of_width[D]]++;
             int64_t gp = b.path_base + lp;
             int64_t r = b.rec_off + lp * (D + 1);
-            double zprod = 1.0;
-            for (int j = 0; j < p.d; ++j) zprod *= o.elems[p.el_off + j].z;
-            P->bias += p.val * zprod;
+            const bool pr = p.leaf2 >= 0;
+            // element j of the path sits in slot j, except a pair's element
+            // (its last), which sits in the last slot after any padding
+            auto slot_of = [&](int j) { return (pr && j == p.d - 1) ? D - 1 : j; };
+            double zprod = 1.0;  // pairs: the shared elements only
+            for (int j = 0; j < (pr ? p.d - 1 : p.d); ++j) zprod *= o.elems[p.el_off + j].z;
             P->sum_unique += p.d;
             P->path_leaf[gp] = p.leaf;
-            P->path_zprod[gp] = zprod;
             P->path_val[gp] = p.val;
+            if (pr) {
+                P->bias += p.val_a * zprod * p.z_a + p.val_b * zprod * p.z_b;
+                P->path_zprod[gp] = zprod * p.z_a;
+                P->pair_leaf2[gp] = p.leaf2;
+                P->pair_zprod2[gp] = zprod * p.z_b;
+                P->pair_z[2 * gp] = p.z_a;
+                P->pair_z[2 * gp + 1] = p.z_b;
+                P->pair_gslot[gp] = b.slot_base + lp * D + D - 1;
+                ++P->n_pair_paths;
+            } else {
+                P->bias += p.val * zprod;
+                P->path_zprod[gp] = zprod;
+            }
             if (fp64) {
                 P->rec64[r] = {p.val, zprod, 0.f, 0.f, 0u, 0u};
                 for (int j = 0; j < D; ++j) {
@@ -448,26 +566,30 @@ qts_status prepare(int32_t n_trees, const int64_t* off, const int32_t* left, con
                     }
                 }
             } else {
-                P->rec32[r] = {(float)p.val, (float)zprod, 0.f, 0u};
-                for (int j = 0; j < D; ++j) {
-                    if (j < p.d) {
-                        const ElemTmp& m = o.elems[p.el_off + j];
-                        float lo, hi;
-                        const uint32_t bits = elem_bits(m, &lo, &hi);
-                        if (m.is_cat) P->has_cat = true;
-                        P->rec32[r + 1 + j] = {(float)m.z, lo, hi, bits};
-                    } else {
-                        P->rec32[r + 1 + j] = {1.f, -INFINITY, INFINITY, pad_bits};
-                    }
+                if (pr) {
+                    uint32_t tb;
+                    std::memcpy(&tb, &p.theta, 4);
+                    P->rec32[r] = {1.f, (float)(p.val_a - p.alpha), (float)(p.val_b - p.alpha), tb};
+                } else {
+                    P->rec32[r] = {(float)p.val, (float)zprod, 0.f, 0u};
+                }
+                for (int j = 0; j < D; ++j) P->rec32[r + 1 + j] = {1.f, -INFINITY, INFINITY, pad_bits};
+                for (int j = 0; j < p.d; ++j) {
+                    const ElemTmp& m = o.elems[p.el_off + j];
+                    float lo, hi;
+                    uint32_t bits = elem_bits(m, &lo, &hi);
+                    if (m.is_cat) P->has_cat = true;
+                    if (pr && j == p.d - 1) bits |= kPairElem | (p.def_left ? kDefLeft : 0u);
+                    P->rec32[r + 1 + slot_of(j)] = {(float)m.z, lo, hi, bits};
                 }
             }
             int64_t slot0 = b.slot_base + lp * D;
             for (int j = 0; j < p.d; ++j) {
-                P->slot_edge_begin[slot0 + j + 1] = o.elems[p.el_off + j].edge_cnt;
+                P->slot_edge_begin[slot0 + slot_of(j) + 1] = o.elems[p.el_off + j].edge_cnt;
                 double ex = 1.0;  // prod of the other elements' z (no division)
                 for (int l = 0; l < p.d; ++l)
                     if (l != j) ex *= o.elems[p.el_off + l].z;
-                P->slot_zexcl[slot0 + j] = ex;
+                P->slot_zexcl[slot0 + slot_of(j)] = ex;
             }
         }
     }
@@ -481,15 +603,19 @@ qts_status prepare(int32_t n_trees, const int64_t* off, const int32_t* left, con
             Bucket& b = P->buckets[bidx_of_width[D]];
             int64_t lp = cursor[bidx_of_width[D]]++;
             int64_t slot0 = b.slot_base + lp * D;
+            const bool pr = p.leaf2 >= 0;
             for (int j = 0; j < p.d; ++j) {
                 const ElemTmp& m = o.elems[p.el_off + j];
-                int64_t e0 = P->slot_edge_begin[slot0 + j];
+                int64_t e0 = P->slot_edge_begin[slot0 + ((pr && j == p.d - 1) ? D - 1 : j)];
                 for (int a = 0; a < m.edge_cnt; ++a) {
-                    double others = 1.0;
-                    for (int c = 0; c < m.edge_cnt; ++c)
-                        if (c != a) others *= o.edge_w[m.edge_off + c];
+                    double coef = o.edge_cf[m.edge_off + a];
+                    if (std::isnan(coef)) {  // the product of the element's other edge weights
+                        coef = 1.0;
+                        for (int c = 0; c < m.edge_cnt; ++c)
+                            if (c != a) coef *= o.edge_w[m.edge_off + c];
+                    }
                     P->edge_node[e0 + a] = o.edge_node[m.edge_off + a];
-                    P->edge_coef[e0 + a] = others;
+                    P->edge_coef[e0 + a] = coef;
                 }
             }
         }

@@ -129,21 +129,38 @@ extern "C" qts_status qts_autotune(qts_ensemble* e, const float* X, int64_t M, i
     }
     double* g_val = (double*)e->d_work + 4;
     double* g_slot = g_val + P.n_paths;
-    for (const Bucket& b : P.buckets) {
-        const std::string key = cache_key(b.D, F, M);
+    st = ensure_batch_tables(e);  // the forward runs on the pair tables
+    if (st != QTS_OK) {
+        cudaFree(phi);
+        cudaFree(grad);
+        return st;
+    }
+    // the forward runs on the pair tables, the adjoint on the per-leaf tables:
+    // tune each width with that width's bucket of each (where it has one)
+    auto bucket_of = [](const Prepared& Q, int D) -> const Bucket* {
+        for (const Bucket& b : Q.buckets)
+            if (b.D == D) return &b;
+        return nullptr;
+    };
+    for (int D = 1; D <= kMaxD; ++D) {
+        const Bucket* bf = bucket_of(e->bprep, D);
+        const Bucket* bb = bucket_of(P, D);
+        if (!bf && !bb) continue;
+        const std::string key = cache_key(D, F, M);
         auto it = cache.find(key);
         if (it != cache.end()) {
-            const Tune keep = e->tune[b.D];  // the batched-launch tuner's choices stay
-            e->tune[b.D] = it->second;
-            e->tune[b.D].bt_paths = keep.bt_paths;
-            e->tune[b.D].bt_mode = keep.bt_mode;
+            const Tune keep = e->tune[D];  // the batched-launch tuner's choices stay
+            e->tune[D] = it->second;
+            e->tune[D].bt_paths = keep.bt_paths;
+            e->tune[D].bt_mode = keep.bt_mode;
             continue;
         }
-        Tune best = e->tune[b.D];
+        Tune best = e->tune[D];
         float best_ms = 1e30f;
         const int nps[3] = {8, 4, 2};
         for (int np : nps) {
-            if ((np == 8 && b.D > 8) || (np == 4 && b.D > 24)) continue;
+            if (!bf) break;
+            if ((np == 8 && D > 8) || (np == 4 && D > 24)) continue;
             for (int warps : {2, 4, 8}) {
                 for (int paths : {128, 512, 2048}) {
                     for (int sub : {16, 32}) {
@@ -156,7 +173,7 @@ extern "C" qts_status qts_autotune(qts_ensemble* e, const float* X, int64_t M, i
                         t.priv = priv;
                         cudaError_t le = cudaSuccess;
                         const float ms = time_ms([&] {
-                            le = launch_fwd_bucket(e, b, X, Mt, F, qf, qd, phi, t, s);
+                            le = launch_fwd_bucket(e, *bf, X, Mt, F, qf, qd, phi, t, s);
                         }, s, 3);
                         if (le == cudaSuccess && ms < best_ms) {
                             best_ms = ms;
@@ -171,13 +188,14 @@ extern "C" qts_status qts_autotune(qts_ensemble* e, const float* X, int64_t M, i
         // work-item size of the fused forward + adjoint pass (batched launches)
         float best_b = 1e30f;
         for (int paths : {32, 64, 128, 256, 512}) {
+            if (!bb) break;
             Tune t = best;
             t.paths = paths;
             t.sub = 16;
             t.warps = 4;
             cudaError_t le = cudaSuccess;
             const float ms = time_ms([&] {
-                le = launch_bwd_bucket(e, b, X, grad, Mt, F, qf, g_val, g_slot, phi, t, s);
+                le = launch_bwd_bucket(e, *bb, X, grad, Mt, F, qf, g_val, g_slot, phi, t, s);
             }, s, 3);
             if (le == cudaSuccess && ms < best_b) {
                 best_b = ms;
@@ -185,7 +203,7 @@ extern "C" qts_status qts_autotune(qts_ensemble* e, const float* X, int64_t M, i
             }
             cudaGetLastError();
         }
-        e->tune[b.D] = best;
+        e->tune[D] = best;
         cache[key] = best;
     }
     ce = cudaStreamSynchronize(s);

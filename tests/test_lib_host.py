@@ -321,3 +321,43 @@ def test_alg1_program_bit_for_bit():
     assert got["levels"] == levels
     assert np.array_equal(got["records"], rec)
     assert ((rec[:, 6] >> 16) & 127 != 127).any()  # repeated features occur
+
+
+def _pair_count(ens):
+    """Sibling pairs (internal nodes whose two children are leaves) and the sum
+    of their merged path lengths: the features on the way to the node plus the
+    node's own feature."""
+    n = sd = 0
+    for t in range(ens.n_trees):
+        base = int(ens.node_offsets[t])
+        stack = [(0, frozenset())]
+        while stack:
+            v, fs = stack.pop()
+            g = base + v
+            if ens.left[g] < 0:
+                continue
+            l, r = base + int(ens.left[g]), base + int(ens.right[g])
+            f = int(ens.feature[g])
+            if ens.left[l] < 0 and ens.left[r] < 0:
+                n += 1
+                sd += len(fs | {f})
+                continue
+            stack.append((int(ens.left[g]), fs | {f}))
+            stack.append((int(ens.right[g]), fs | {f}))
+    return n, sd
+
+
+@pytest.mark.parametrize("seed,depth,F", [(61, 6, 9), (62, 12, 5), (63, 4, 3), (64, 9, 40)])
+def test_pair_tables_count_and_bias(seed, depth, F):
+    """The batched pass's tables hold each sibling pair as one path: one path
+    fewer per pair, the pair's merged length counted once, every leaf kept, and
+    the same E[f] (the pair element's z is val_A z_A + val_B z_B)."""
+    ens = synth.grow(seed, 7, depth, F, 3000, 1.0, min_rows=2)
+    full = qts.describe(ens)
+    pairs = qts.describe(ens, pairs=True)
+    n_pairs, sd_pairs = _pair_count(ens)
+    assert n_pairs > 0
+    assert pairs["n_leaves"] == full["n_leaves"]
+    assert pairs["n_paths"] == full["n_paths"] - n_pairs
+    assert pairs["sum_unique"] == full["sum_unique"] - sd_pairs
+    assert pairs["expected_value"] == pytest.approx(full["expected_value"], rel=1e-12, abs=1e-12)
