@@ -335,6 +335,7 @@ def run_ours(args, rank, world, local):
         acc = accuracy_check(works, infos, {"batched": (phi, dl, dz), "plain": (phi_p, dl_p, dz_p),
                                      "plain_fused": (phi_f, dl_f, dz_f)})
         fixed = fixed_workloads(qts, dev, stream, flush)
+        small = small_requests(qts, dev, stream, flush)
         cpu, cpu_quad = cpu_baseline(works, budget_s=args.cpu_seconds)
         pk = peaks()
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -377,6 +378,7 @@ def run_ours(args, rank, world, local):
                     "steps": len(e2e_ms), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "accuracy": acc,
             "fixed_workloads": fixed,
+            "small_requests": small,
             "cpu_baseline": cpu,
             "cpu_quadrature": cpu_quad,
             "gpu_launches": int(n_kern * args.steps),
@@ -467,6 +469,48 @@ def accuracy_check(works, infos, arms, rows_per=2, leaves_per=16):
         out[name] = {"max_rel_err_phi": e_phi, "max_rel_err_grad": e_grad}
     out["oracle_seconds"] = round(time.time() - t0, 1)
     return out
+
+
+def small_requests(qts, dev, stream, flush, n_ens=64, reps=10):
+    """Where one persistent launch pays: 64 small requests (the batch's size
+    draws with at most 256 samples and 5% of the trees each), fused forward +
+    adjoint as one batched call, as one fused call per request, and as the
+    plain per-request kernels."""
+    import torch
+
+    import synth
+
+    works = synth.batch_config(n_ens=n_ens, seed=synth.SEED_BASE + 5, max_samples=256, tree_scale=0.05)
+    ens = [qts.Ensemble.from_arrays(w.ens) for w in works]
+    X = [torch.from_numpy(w.X).to(dev) for w in works]
+    G = [torch.from_numpy(w.grad_phi).to(dev) for w in works]
+    mk = lambda: [dict(ens=e, X=x, grad_phi=g, phi=torch.empty((w.M, w.F + 1), dtype=torch.float64, device=dev),
+                       d_leaf=torch.empty(e.n_nodes, dtype=torch.float64, device=dev),
+                       d_z=torch.empty(e.n_nodes, dtype=torch.float64, device=dev))
+                  for e, x, g, w in zip(ens, X, G, works)]
+    items = mk()
+    reqs = qts.make_requests(items)
+    singles = [qts.make_requests([it]) for it in mk()]
+
+    def plain():
+        for it in items:
+            qts.shap_values(it["ens"], it["X"], N_QUAD, out=it["phi"])
+            qts.shap_backward(it["ens"], it["X"], it["grad_phi"], N_QUAD, d_leaf=it["d_leaf"], d_z=it["d_z"])
+
+    t_b = time_arm(lambda: qts.batched_fwd_bwd(reqs, N_QUAD), reps, 3, stream, flush)
+    t_s = time_arm(lambda: [qts.batched_fwd_bwd(r, N_QUAD) for r in singles], reps, 3, stream, flush)
+    t_p = time_arm(plain, reps, 3, stream, flush)
+    for e in ens:
+        e.sync_status()
+        e.close()
+    U = units(works)
+    ms = {k: float(np.median(v)) for k, v in (("batched", t_b), ("plain_fused", t_s), ("plain", t_p))}
+    return {"requests": len(works), "sample_trees_per_step": U, "steps": reps,
+            "batched": {"ms": ms["batched"], "value": U / (ms["batched"] / 1e3)},
+            "plain_fused": {"ms": ms["plain_fused"], "value": U / (ms["plain_fused"] / 1e3)},
+            "plain": {"ms": ms["plain"], "value": U / (ms["plain"] / 1e3)},
+            "batched_over_plain_fused": ms["plain_fused"] / ms["batched"],
+            "batched_over_plain": ms["plain"] / ms["batched"]}
 
 
 def fixed_workloads(qts, dev, stream, flush, reps=5):

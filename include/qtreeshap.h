@@ -289,8 +289,9 @@ qts_status qts_batched_fwd_bwd(int32_t n_requests, const qts_request *reqs, int3
  * set of requests by timing its persistent kernel on the requests' own data (the
  * autotuner of the batched form; the paper has no batching).  For every bucket
  * width that carries at least 1% of the batch's work it times, with that
- * width's work items alone in the launch, the paths per work item (half, once
- * and twice the default) and, where the fused pass packs two samples per lane,
+ * width's work items alone in the launch, the paths per work item (one, two,
+ * four and eight times the default, at most 4,096) and, where the fused pass
+ * packs two samples per lane,
  * the sample mapping (each warp its own 64 samples, or the block's warps sharing
  * 64 samples and splitting the paths), and keeps the fastest.  The choices are
  * stored in each request's ensemble and used by later batched calls that

@@ -423,10 +423,6 @@ void batch_forget(const qts_ensemble* e) {
 
 // widths 40, 48, 56 and 64 (bucket widths) are classes of their own
 int batch_class(int D) { return D <= 6 ? 8 : D <= 10 ? 12 : (D <= 16 ? 16 : (D <= 32 ? 32 : D)); }
-constexpr int kClasses = 8;
-static int class_index(int cls) {
-    return cls == 8 ? 0 : cls == 12 ? 1 : cls == 16 ? 2 : cls == 32 ? 3 : cls == 40 ? 4 : cls == 48 ? 5 : cls == 56 ? 6 : 7;
-}
 // shared memory one block of a class may use and still reach its blocks per SM
 static size_t class_smem_budget(int cls) {
     const size_t sm = 227 * 1024;
@@ -494,10 +490,11 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
         SegDev d;
         double cost;  // per item
         int cls;
+        int64_t tile;  // floats of its phi region
+        int bin;       // tile-size bin: one launch per (class, bin)
     };
     std::vector<SegHost> segs;
     std::vector<ReqDev> rd(n);
-    int64_t tile_need[kClasses] = {0, 0, 0, 0, 0, 0, 0, 0};  // per register class index
     const int sub = 32;                        // paths per staged sub-chunk
     for (int r = 0; r < n; ++r) {
         const qts_request& R = reqs[r];
@@ -512,7 +509,7 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
         double* g_slot = grad ? g_val + 2 * e->bprep.n_paths : nullptr;
         for (const Bucket& b : e->bprep.buckets) {
             if (ov && ov->only_width > 0 && b.D != ov->only_width) continue;
-            const int cls = batch_class(b.D), ci = class_index(cls);
+            const int cls = batch_class(b.D);
             const Tune& tn = e->tune[b.D];
             int mode = R.F + 1 <= kPrivRows ? 1 : 0;
             if (grad && pair_width(b.D) &&
@@ -520,7 +517,6 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
                 const int want = ov && ov->mode[b.D] ? ov->mode[b.D] : tn.bt_mode;
                 mode = want == 3 ? 3 : 2;
             }
-            tile_need[ci] = std::max(tile_need[ci], tile_floats_for(mode, R.F));
             const int per_item = item_samples(mode);
             const int n_tiles = (int)((R.M + per_item - 1) / per_item);
             SegHost s;
@@ -537,24 +533,33 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
             s.d.pad = 0;
             s.cost = (double)s.d.paths * b.D * (grad ? 12 : 4);
             s.cls = cls;
+            // a launch sizes its shared memory for its widest tile, and whatever
+            // shared memory a block does not take stays L1 (which serves the x and
+            // grad_phi loads): requests of one class are launched by tile size
+            s.tile = tile_floats_for(mode, R.F);
+            const int64_t tb = s.tile * 4;
+            s.bin = tb <= 48 * 1024 ? 0 : tb <= 80 * 1024 ? 1 : 2;
             segs.push_back(s);
         }
     }
-    // group by kernel class, heaviest items first within a class
+    // one launch per (kernel class, tile bin), heaviest items first within it
     std::stable_sort(segs.begin(), segs.end(), [](const SegHost& a, const SegHost& b) {
         if (a.cls != b.cls) return a.cls < b.cls;
+        if (a.bin != b.bin) return a.bin < b.bin;
         return a.cost > b.cost;
     });
     std::vector<int> cls_list;
-    std::vector<int64_t> cls_items, cls_first_seg;
+    std::vector<int64_t> cls_items, cls_first_seg, cls_tile;
     int64_t item = 0;
     for (size_t i = 0; i < segs.size(); ++i) {
-        if (cls_list.empty() || cls_list.back() != segs[i].cls) {
+        if (cls_list.empty() || cls_list.back() != segs[i].cls || segs[i - 1].bin != segs[i].bin) {
             cls_list.push_back(segs[i].cls);
             cls_first_seg.push_back((int64_t)i);
             cls_items.push_back(0);
+            cls_tile.push_back(0);
             item = 0;
         }
+        cls_tile.back() = std::max(cls_tile.back(), segs[i].tile);
         segs[i].d.item_begin = item;
         const int64_t chunks = (segs[i].d.n_paths + segs[i].d.paths - 1) / segs[i].d.paths;
         item += chunks * segs[i].d.n_tiles;
@@ -617,7 +622,7 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
         a.reqs = d_reqs;
         a.n_items = cls_items[c];
         a.counter = d_cnt + c;
-        a.tile_floats = std::max<int64_t>(tile_need[class_index(cls)], kTileLd);
+        a.tile_floats = std::max<int64_t>(cls_tile[c], kTileLd);
         a.sub = sub;
         a.q = q;
         const size_t smem = batch_smem_bytes(a.tile_floats, sub, cls);
@@ -823,8 +828,8 @@ extern "C" qts_status qts_batched_autotune(int32_t n, const qts_request* reqs, i
         float best = 1e30f;
         for (int mode : {2, 3}) {
             if (mode == 3 && !packed[D]) continue;
-            for (int mult : {1, 2, 4}) {  // base / 2, base, base * 2
-                const int paths = std::max(32, std::min(2048, base * mult / 2 / 32 * 32));
+            for (int mult : {1, 2, 4, 8}) {  // base, twice, four and eight times
+                const int paths = std::max(32, std::min(4096, base * mult / 32 * 32));
                 ov.paths[D] = paths;
                 ov.mode[D] = packed[D] ? mode : 0;
                 float ms = 0.f;

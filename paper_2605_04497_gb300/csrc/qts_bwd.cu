@@ -109,18 +109,18 @@ __global__ void __launch_bounds__(256) bwd_kernel(BwdArgs a) {
         (const Rec*)a.rec, p0, p1, a.sub, st0, st1, bars, s_phase, &s_flag, a.status,
         [&](int64_t p, const Rec* r) {
             double* gsl = a.g_slot + p * D;
-            double* gv = a.g_val + p;
+            double* gv = a.g_val + (FP64 ? p : 2 * p);  // FP32: pair tables, two sums per path
             if constexpr (FP64) {
                 if (has_nan) bwd_path_f64<D, true>(r, xs, gs, lane, a.qd, gsl, gv);
                 else bwd_path_f64<D, false>(r, xs, gs, lane, a.qd, gsl, gv);
             } else {
                 const SmemCols xr{xs, lane}, gr{gs, lane};
                 if constexpr (D <= 16) {
-                    if (has_nan) bwd_path_f32_pk<D, true, WITH_PHI ? kPhiAtomic : kPhiNone>(r, xr, gr, ps, lane, a.q, gsl, gv);
-                    else bwd_path_f32_pk<D, false, WITH_PHI ? kPhiAtomic : kPhiNone>(r, xr, gr, ps, lane, a.q, gsl, gv);
+                    if (has_nan) bwd_path_f32_pk<D, true, WITH_PHI ? kPhiAtomic : kPhiNone, SmemCols, SmemCols, true>(r, xr, gr, ps, lane, a.q, gsl, gv);
+                    else bwd_path_f32_pk<D, false, WITH_PHI ? kPhiAtomic : kPhiNone, SmemCols, SmemCols, true>(r, xr, gr, ps, lane, a.q, gsl, gv);
                 } else {
-                    if (has_nan) bwd_path_f32<D, NP, true, WITH_PHI ? kPhiAtomic : kPhiNone, false>(r, xr, gr, ps, lane, a.q, gsl, gv);
-                    else bwd_path_f32<D, NP, false, WITH_PHI ? kPhiAtomic : kPhiNone, false>(r, xr, gr, ps, lane, a.q, gsl, gv);
+                    if (has_nan) bwd_path_f32<D, NP, true, WITH_PHI ? kPhiAtomic : kPhiNone, false, SmemCols, SmemCols, true>(r, xr, gr, ps, lane, a.q, gsl, gv);
+                    else bwd_path_f32<D, NP, false, WITH_PHI ? kPhiAtomic : kPhiNone, false, SmemCols, SmemCols, true>(r, xr, gr, ps, lane, a.q, gsl, gv);
                 }
             }
         });
@@ -267,8 +267,9 @@ cudaError_t launch_bwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
     QuadD qd;
     make_quad(q.n, nullptr, &qd);
     BwdArgs a;
+    // FP32: the pair tables (two adjoint sums per path), FP64: the per-leaf tables
     a.rec = fp64 ? (const void*)((const Rec64*)e->d_rec + b.rec_off)
-                 : (const void*)((const Rec32*)e->d_rec + b.rec_off);
+                 : (const void*)((const Rec32*)e->bdev.rec + b.rec_off);
     a.n_paths = b.n_paths;
     const bool with_phi = phi != nullptr && !fp64;
     a.sub = std::max(1, tn.sub);
@@ -280,8 +281,8 @@ cudaError_t launch_bwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
     a.G = grad;
     a.M = M;
     a.F = F;
-    a.cat = e->prep.has_cat ? 1 : 0;
-    a.g_val = g_val + b.path_base;
+    a.cat = (fp64 ? e->prep.has_cat : e->bprep.has_cat) ? 1 : 0;
+    a.g_val = g_val + (fp64 ? 1 : 2) * b.path_base;
     a.g_slot = g_slot + b.slot_base;
     a.phi = phi;
     a.status = e->d_status;
@@ -416,13 +417,20 @@ extern "C" qts_status qts_shap_backward(qts_ensemble* e, const float* X, int64_t
     cudaStream_t s = (cudaStream_t)stream;
     QuadF qf;
     if (!make_quad(n_quad, &qf, nullptr)) return fail(QTS_ERR_ARG, "quadrature rule");
-    const Prepared& P = e->prep;
-    const size_t bytes = sizeof(double) * (size_t)(4 + P.n_paths + P.n_slots);
+    // FP32 runs on the pair tables (two sums per path), FP64 on the per-leaf tables
+    const bool fp64 = (e->flags & QTS_FLAG_FP64) != 0;
+    if (!fp64) {
+        st = ensure_batch_tables(e);
+        if (st != QTS_OK) return st;
+    }
+    const Prepared& P = fp64 ? e->prep : e->bprep;
+    const int per_path = fp64 ? 1 : 2;
+    const size_t bytes = sizeof(double) * (size_t)(4 + per_path * P.n_paths + P.n_slots);
     st = ensure_workspace(e, bytes);
     if (st != QTS_OK) return st;
     double* gb = (double*)e->d_work;
     double* g_val = gb + 4;
-    double* g_slot = g_val + P.n_paths;
+    double* g_slot = g_val + per_path * P.n_paths;
     cudaError_t ce = cudaMemsetAsync(e->d_work, 0, bytes, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "workspace clear");
     if (M > 0) {
@@ -430,7 +438,8 @@ extern "C" qts_status qts_shap_backward(qts_ensemble* e, const float* X, int64_t
             ce = launch_bwd_bucket(e, b, X, grad_phi, M, F, qf, g_val, g_slot, nullptr, e->tune[b.D], s);
             if (ce != cudaSuccess) return cuda_fail(ce, "adjoint kernel launch");
         }
-        ce = launch_bwd_epilogue(e, grad_phi, M, F, g_val, g_slot, d_leaf, d_z, gb, s);
+        ce = fp64 ? launch_bwd_epilogue(e, grad_phi, M, F, g_val, g_slot, d_leaf, d_z, gb, s)
+                  : launch_bwd_epilogue_pairs(e, grad_phi, M, F, g_val, g_slot, d_leaf, d_z, gb, s);
     } else {
         ce = cudaMemsetAsync(d_leaf, 0, sizeof(double) * e->n_nodes, s);
         if (ce == cudaSuccess) ce = cudaMemsetAsync(d_z, 0, sizeof(double) * e->n_nodes, s);

@@ -254,14 +254,15 @@ __device__ __forceinline__ void flush_path_grads(T (&dz)[D], T dval, int lane, d
 
 // RECOMP: recompute a_j in the backward sweep instead of keeping it in
 // registers (one more FMA per element and node, a third fewer registers).
-template <int D, int NP, bool HAS_NAN, int PHI, bool RECOMP, typename XR, typename GR>
+template <int D, int NP, bool HAS_NAN, int PHI, bool RECOMP, typename XR, typename GR, bool PAIRS = false>
 __device__ __forceinline__ void bwd_path_f32(const Rec32* __restrict__ r, const XR& xr, const GR& gr,
                                              float* ps, int lane, const QuadF& q, double* g_slot_p,
                                              double* g_val_p) {
     constexpr int K = NP / 2;
     constexpr int DA = RECOMP ? 1 : D;
     const float val = r[0].z;
-    float dd[D], uu[D], acc1[D], acc2[D];
+    const bool pair = PAIRS && (r[D].bits & kPairElem) != 0;
+    float dd[D], uu[D], acc1[D], acc2[D], acc3 = 0.f;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
         const Rec32 e = r[1 + j];
@@ -269,6 +270,7 @@ __device__ __forceinline__ void bwd_path_f32(const Rec32* __restrict__ r, const 
         const float x = xr(f);
         const bool o = satisfies<HAS_NAN>(x, e.lo, e.hi, e.bits);
         dd[j] = (o ? 1.f : 0.f) - e.z;
+        if (j == D - 1 && pair) dd[j] = pair_d(x, e, r[0]);
         uu[j] = gr(f) * dd[j];
         acc1[j] = 0.f;
         acc2[j] = 0.f;
@@ -296,6 +298,10 @@ __device__ __forceinline__ void bwd_path_f32(const Rec32* __restrict__ r, const 
                     PU[j + 1][k] = fma2(PU[j][k], a, mul2(u2, P[j][k]));
                 }
             }
+        }
+        if constexpr (PAIRS && D > 1) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc3 += PU[D - 1][k].x + PU[D - 1][k].y;
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -336,6 +342,20 @@ __device__ __forceinline__ void bwd_path_f32(const Rec32* __restrict__ r, const 
         dval = fmaf(uu[j], acc1[j], dval);
         dz[j] = val * (acc2[j] - gr(f) * acc1[j]);
         phi_add<PHI>(ps, f * kTileLd + lane, val * dd[j] * acc1[j]);
+    }
+    if constexpr (PAIRS) {
+        if (pair) {  // val = 1: dval becomes o_A K, a second sum o_B K goes to g_val_p[1]
+            const Rec32 e = r[D];
+            const int f = feat_of(e.bits);
+            bool oa, ob;
+            pair_sides(xr(f), e, r[0], &oa, &ob);
+            const float k = acc3 - acc2[D - 1] + gr(f) * acc1[D - 1];
+            dval = oa ? k : 0.f;
+            float rb = ob ? k : 0.f;
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) rb += __shfl_xor_sync(0xffffffffu, rb, off);
+            if (lane == 0) atomicAdd(g_val_p + 1, (double)rb);
+        }
     }
     flush_path_grads<D, float>(dz, dval, lane, g_slot_p, g_val_p);
 }

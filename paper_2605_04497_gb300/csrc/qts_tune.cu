@@ -112,7 +112,10 @@ extern "C" qts_status qts_autotune(qts_ensemble* e, const float* X, int64_t M, i
     make_quad(8, &qf, &qd);
     double* phi = nullptr;
     float* grad = nullptr;
-    const Prepared& P = e->prep;
+    // the FP32 forward and adjoint run on the pair tables
+    st = ensure_batch_tables(e);
+    if (st != QTS_OK) return st;
+    const Prepared& P = e->bprep;
     cudaError_t ce = cudaMalloc(&phi, sizeof(double) * Mt * (F + 1));
     if (ce == cudaSuccess) ce = cudaMalloc(&grad, sizeof(float) * Mt * (F + 1));
     if (ce == cudaSuccess) ce = cudaMemsetAsync(grad, 0, sizeof(float) * Mt * (F + 1), s);
@@ -121,31 +124,20 @@ extern "C" qts_status qts_autotune(qts_ensemble* e, const float* X, int64_t M, i
         cudaFree(grad);
         return cuda_fail(ce, "autotune scratch");
     }
-    st = ensure_workspace(e, sizeof(double) * (size_t)(4 + P.n_paths + P.n_slots));
+    st = ensure_workspace(e, sizeof(double) * (size_t)(4 + 2 * P.n_paths + P.n_slots));
     if (st != QTS_OK) {
         cudaFree(phi);
         cudaFree(grad);
         return st;
     }
     double* g_val = (double*)e->d_work + 4;
-    double* g_slot = g_val + P.n_paths;
-    st = ensure_batch_tables(e);  // the forward runs on the pair tables
-    if (st != QTS_OK) {
-        cudaFree(phi);
-        cudaFree(grad);
-        return st;
-    }
-    // the forward runs on the pair tables, the adjoint on the per-leaf tables:
-    // tune each width with that width's bucket of each (where it has one)
-    auto bucket_of = [](const Prepared& Q, int D) -> const Bucket* {
-        for (const Bucket& b : Q.buckets)
-            if (b.D == D) return &b;
-        return nullptr;
-    };
+    double* g_slot = g_val + 2 * P.n_paths;
     for (int D = 1; D <= kMaxD; ++D) {
-        const Bucket* bf = bucket_of(e->bprep, D);
-        const Bucket* bb = bucket_of(P, D);
-        if (!bf && !bb) continue;
+        const Bucket* bf = nullptr;
+        for (const Bucket& b : P.buckets)
+            if (b.D == D) bf = &b;
+        const Bucket* bb = bf;
+        if (!bf) continue;
         const std::string key = cache_key(D, F, M);
         auto it = cache.find(key);
         if (it != cache.end()) {

@@ -20,6 +20,8 @@ Cases (synthetic inputs from `synth`):
   alg1-xgb, alg1-deep20, alg1-adultlike
                      qts_shap_values_alg1 (depth-first form) on the same inputs as
                      forward-xgb, forward-deep20 and forward-adultlike
+  batch64            qts_batched_fwd_bwd on the benchmark's 64-ensemble batch (one
+                     graph launch per call; the bench's default parameters)
 Prints the median CUDA-event time per call and the algorithmic FP32-pipe
 operation rate (4 ops per sample x element x node forward, 11 adjoint/fused;
 4 per sample x edge x node for the depth-first form).
@@ -47,11 +49,13 @@ def main():
     ap.add_argument("case", choices=["forward-xgb", "adjoint-xgb", "interactions-500", "fused-xgb",
                                      "fused-deep", "adjoint-deep", "interactions3-500",
                                      "forward-adultlike", "forward-deep20", "alg1-xgb", "alg1-deep20",
-                                     "alg1-adultlike", "orders-covtypelike"])
+                                     "alg1-adultlike", "orders-covtypelike", "batch64"])
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     if args.case == "orders-covtypelike":
         return orders_case(args.reps)
+    if args.case == "batch64":
+        return batch64_case(args.reps)
     if args.case.endswith("-deep"):
         seed = synth.SEED_BASE + 4
         trees, depth, feats, samples = synth.batch_draw(seed, 64)
@@ -113,6 +117,32 @@ def main():
     print(f"{args.case}: {ms:.3f} ms/call, {w.M * w.ens.n_trees / ms * 1e3:.3e} sample*trees/s"
           + (f", {work / ms / 1e9:.2f} Tops/s algorithmic" if ops else ""))
     E.close()
+
+
+def batch64_case(reps):
+    """The 64-ensemble batch: one batched call to warm up, then `reps` calls."""
+    import torch
+
+    import synth
+    import paper_2605_04497_gb300 as qts
+
+    works = synth.batch_config()
+    ens = [qts.Ensemble.from_arrays(w.ens) for w in works]
+    items = [dict(ens=e, X=torch.from_numpy(w.X).cuda(), grad_phi=torch.from_numpy(w.grad_phi).cuda(),
+                  phi=torch.empty((w.M, w.F + 1), dtype=torch.float64, device="cuda"),
+                  d_leaf=torch.empty(e.n_nodes, dtype=torch.float64, device="cuda"),
+                  d_z=torch.empty(e.n_nodes, dtype=torch.float64, device="cuda")) for e, w in zip(ens, works)]
+    reqs = qts.make_requests(items)
+    qts.batched_fwd_bwd(reqs)
+    torch.cuda.synchronize()
+    for _ in range(reps):
+        qts.batched_fwd_bwd(reqs)
+        torch.cuda.synchronize()
+        print(f"batch64: persistent kernels {qts.batched_last_kernel_ms():.1f} ms, "
+              f"{qts.batched_kernel_count()} launches per call")
+    for e in ens:
+        e.sync_status()
+        e.close()
 
 
 def orders_case(reps):
