@@ -35,12 +35,10 @@ UNIT = "sample·trees/s"
 WORKLOAD = ("batch64: 64 ensembles, trees log-U[10,2000], depth U{3..16}, F log-U[8,200], "
             "M log-U[1,50000], covers from min(100000, 20*2^depth) rows, grad_phi ~N(0,1), seed 20260504")
 N_QUAD = 8
-# DRAM bytes (read + write) per step of the persistent launches, from an ncu
-# capture of one kernel on a small request scaled by the units processed; valid
-# only while the kernel sources hash to TRAFFIC_HASH, otherwise reported as null.
-TRAFFIC_BYTES = (1.684 + 0.799 + 12.541 + 4.953 + 11.343 + 3.827) * 1e9
-TRAFFIC_HASH = "f43243ce70c89602"
-KERNEL_SOURCES = ("qts_batch.cu", "qts_paths.cuh", "qts_device.cuh", "qts_internal.h")
+# DRAM traffic per step of the persistent launches is not reported: the
+# counters are taken on one kernel of a one-request case (tens of MB per
+# launch), and the batch's reads follow its table sizes, not its work, so they
+# do not scale to the step by the units processed.
 # FP32-pipe operations per (sample, merged path element, quadrature node)
 OPS_FUSED = 11   # forward + adjoint in one pass
 OPS_FWD = 4      # forward alone
@@ -104,16 +102,6 @@ def parse_clock_rows(rows):
     reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
     return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
             "reasons": reasons, "samples": len(rows)}
-
-
-def kernel_hash() -> str:
-    import hashlib
-
-    h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2605_04497_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
 
 
 def fp32_peak_tops(sms: int, mhz: float) -> float:
@@ -362,8 +350,9 @@ def run_ours(args, rank, world, local):
                          "kernel": "batch_kernel<8>, <12>, <16> (persistent fused forward + adjoint, one launch per register class)",
                          "achieved": achieved, "peak": peak, "unit": "Tops/s (FP32 pipe lane-ops)",
                          "frac": achieved / peak,
-                         "traffic": TRAFFIC_BYTES if kernel_hash() == TRAFFIC_HASH else None,
-                         "traffic_unit": "DRAM bytes per step (the persistent launches), scaled from a one-request capture",
+                         "traffic": None,
+                         "traffic_note": "ALU-bound: one-request captures read tens of MB per launch (0.01% of HBM "
+                                         "bandwidth); not scaled to the batch",
                          "peak_basis": f"{sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (max SM clock)",
                          "algorithmic_ops_per_launch": alg_ops,
                          "ops_basis": "11 FP32-pipe ops per (sample, path element, node) of the pass's tables, "
