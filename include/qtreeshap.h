@@ -130,7 +130,8 @@ qts_status qts_load_ensemble_cat(int32_t n_trees, const int64_t *tree_node_offse
 /*
  * qts_update_params - replace edge weights and leaf values (same topology) and
  * rebuild the path tables (Sec. 2).  z, leaf_value: host, one entry per node.
- * Synchronous.  Errors as qts_load_ensemble.
+ * Synchronous.  The sibling-pair tables of the FP32 calls are dropped and built
+ * again on the next call that needs them.  Errors as qts_load_ensemble.
  */
 qts_status qts_update_params(qts_ensemble *ens, const float *z, const float *leaf_value);
 
@@ -144,7 +145,14 @@ qts_status qts_update_params(qts_ensemble *ens, const float *z, const float *lea
  *           (the bias, so that sum_f phi[s][f] = f(x_s))
  * Per-path arithmetic is FP32 (FP64 with QTS_FLAG_FP64); contributions are
  * accumulated in FP32 over at most a few thousand paths, then in FP64 across
- * path chunks and trees.
+ * path chunks and trees.  With M <= 16 lanes are (path, sample) pairs instead
+ * of one sample per lane.
+ * FP32 ensembles run on a second set of path tables in which each pair of
+ * sibling leaves of a numerical split is one path (see qts_get_batch_info);
+ * it is built by the first FP32 forward, adjoint or batched call (host
+ * preparation, cudaMalloc and synchronous copies, about 60% more device memory
+ * than the per-leaf tables), so that first call must not be inside a stream
+ * capture; later calls only enqueue on `stream`.
  */
 qts_status qts_shap_values(qts_ensemble *ens, const float *X, int64_t M, int32_t F,
                            int32_t n_quad, double *phi, qts_stream_t stream);
@@ -253,6 +261,8 @@ qts_status qts_shap_interactions_noalloc(qts_ensemble *ens, const float *X, int6
  * shap_as_weighted_banzhafs with the same n_quad rule, recomputing per-path
  * products instead of storing them.
  *   grad_phi device, M x (F+1) fp32 (column F weights the bias E[f]).
+ * FP32 ensembles run on the sibling-pair tables (built on first use, as for
+ * qts_shap_values); a pair's dL/dval is split over its two leaves exactly.
  */
 qts_status qts_shap_backward(qts_ensemble *ens, const float *X, int64_t M, int32_t F,
                              int32_t n_quad, const float *grad_phi, double *d_leaf, double *d_z,
