@@ -296,6 +296,15 @@ def run_ours(args, rank, world, local):
                 qts.shap_values(it["ens"], it["X"], N_QUAD, out=phi_p[k])
 
         fwd_ms = time_arm(plain_forward, aux, 1, stream, flush)
+        # the same batched pass with Thm 2's point count per path width
+        # (n_quad = EXACT_NODES: ceil(w / 2) points, exact at every width)
+        phi_x, dl_x, dz_x = outputs()
+        reqs_x = qts.make_requests([dict(ens=e, X=x, grad_phi=g, phi=p, d_leaf=a, d_z=b)
+                                    for e, x, g, p, a, b in zip(ens, X, G, phi_x, dl_x, dz_x)])
+        exact_ms = time_arm(lambda: qts.batched_fwd_bwd(reqs_x, qts.EXACT_NODES), aux, 1, stream, flush)
+        # node work (sample x element x point) with these point counts and with 8
+        node_work = [sum(w.M * n * D * k(D) for w, b in zip(works, binfos) for D, n in b["buckets"])
+                     for k in (qts.exact_nodes, lambda D: N_QUAD)]
         torch.cuda.synchronize()
         for e in ens:
             e.sync_status()
@@ -321,7 +330,8 @@ def run_ours(args, rank, world, local):
 
         # accuracy of every arm against the FP64 oracle (outside timing)
         acc = accuracy_check(works, infos, {"batched": (phi, dl, dz), "plain": (phi_p, dl_p, dz_p),
-                                     "plain_fused": (phi_f, dl_f, dz_f)})
+                                     "plain_fused": (phi_f, dl_f, dz_f),
+                                     "batched_exact_nodes": (phi_x, dl_x, dz_x)})
         fixed = fixed_workloads(qts, dev, stream, flush)
         small = small_requests(qts, dev, stream, flush)
         cpu, cpu_quad = cpu_baseline(works, budget_s=args.cpu_seconds)
@@ -367,6 +377,9 @@ def run_ours(args, rank, world, local):
             "plain_fused": arm(fused_ms, "per request: the same fused forward + adjoint pass, one graph launch each"),
             "plain": arm(plain_ms, "per request: forward launches + adjoint launches + epilogue"),
             "plain_forward": arm(fwd_ms, "per request: forward launches only (phi, no gradients)"),
+            "batched_exact_nodes": dict(arm(exact_ms, "batched, n_quad = EXACT_NODES: per path width w, "
+                                                      "ceil(w/2) Gauss-Legendre points (Thm 2), exact at every width"),
+                                        node_work_vs_8_points=node_work[0] / node_work[1]),
             "e2e": {"value": U / (float(np.mean(e2e_ms)) / 1e3), "unit": UNIT, "ms_per_step": float(np.mean(e2e_ms)),
                     "steps": len(e2e_ms), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "accuracy": acc,
@@ -536,6 +549,11 @@ def fixed_workloads(qts, dev, stream, flush, reps=5):
         rec = {"what": kind, "trees": w.ens.n_trees, "M": w.M, "F": w.F, "paths": E.info()["n_paths"],
                "ms": t, "sample_trees_per_s": w.M * w.ens.n_trees / (t / 1e3)}
         if kind == "phi":
+            # the same call with Thm 2's point count per path width
+            ex = lambda: qts.shap_values(E, Xd, qts.EXACT_NODES, out=res)
+            rec["ms_exact_nodes"] = float(np.median(time_arm(ex, reps if name != "deep-depth20" else 3, 1,
+                                                             stream, flush)))
+            E.sync_status()
             # 4 FP32-pipe ops per (sample, merged element, node): on the
             # leaves' paths (the method's work) and on the pair tables (executed)
             ops = OPS_FWD * N_QUAD * E.info()["sum_unique"] * w.M

@@ -64,6 +64,14 @@ typedef enum qts_status {
 #define QTS_MAX_FEATURES 832 /* the kernels keep a sample tile and an accumulator tile of F + 1
                                 rows in shared memory (F = 784: Fashion-MNIST-shaped models) */
 #define QTS_MAX_QUAD 32
+/* n_quad = QTS_NQ_EXACT: per bucket of paths with at most w unique features,
+   the fewest Gauss-Legendre points that make an order-s quantity exact,
+   ceil((w - s + 1) / 2) (Thm 2; qts_exact_nodes).  The first-order, adjoint and
+   batched calls choose it per bucket, so short paths take fewer points than
+   long ones; the interaction and depth-first calls choose it once, from the
+   ensemble's widest path.  Unlike a fixed n_quad it is exact for every width
+   up to QTS_MAX_UNIQUE_FEATURES_PER_PATH (32 points at width 64). */
+#define QTS_NQ_EXACT 0
 #define QTS_MAX_FEATURES_ORDER3 128
 #define QTS_MAX_CATEGORIES 64 /* categories 0..63 of a categorical split */
 
@@ -140,7 +148,8 @@ qts_status qts_update_params(qts_ensemble *ens, const float *z, const float *lea
  * shap_as_weighted_banzhafs, Alg. 1 with s = 1).
  *   X       device, M x F fp32 row-major
  *   M       samples (>= 0; 0 is a no-op), F must equal the ensemble's n_features
- *   n_quad  Gauss-Legendre points, 1..QTS_MAX_QUAD (8 is the fast path)
+ *   n_quad  Gauss-Legendre points, 1..QTS_MAX_QUAD (8 is the fast path), or
+ *           QTS_NQ_EXACT: ceil(w / 2) points for the paths of width w
  *   phi     device, M x (F+1) fp64, overwritten; phi[s][F] = E[f] = sum_v R_empty^v
  *           (the bias, so that sum_f phi[s][f] = f(x_s))
  * Per-path arithmetic is FP32 (FP64 with QTS_FLAG_FP64); contributions are
@@ -328,9 +337,13 @@ qts_status qts_batched_autotune(int32_t n_requests, const qts_request *reqs, int
  *   n_paths       paths, pairs counted once
  *   sum_unique    sum over paths of their unique features (the work unit)
  *   n_pair_paths  paths that stand for two leaves
+ *   n_buckets     number of path-width buckets (at most 32)
+ *   bucket_width, bucket_paths  host, 32 entries each: width and path count of
+ *                 each bucket (entries past n_buckets are left as they are)
  * Any output pointer may be NULL.
  */
-qts_status qts_get_batch_info(qts_ensemble *ens, int64_t *n_paths, int64_t *sum_unique, int64_t *n_pair_paths);
+qts_status qts_get_batch_info(qts_ensemble *ens, int64_t *n_paths, int64_t *sum_unique, int64_t *n_pair_paths,
+                              int32_t *n_buckets, int32_t *bucket_width, int64_t *bucket_paths);
 
 /* Number of kernels in the graph of the calling thread's last batched call. */
 int32_t qts_batched_kernel_count(void);
@@ -451,6 +464,15 @@ qts_status qts_describe_alg1_program(int32_t n_trees, const int64_t *tree_node_o
 
 /* Gauss-Legendre nodes/weights on [0,1] used by the kernels (fp64, ascending). */
 qts_status qts_gauss_legendre(int32_t n, double *t, double *w);
+
+/*
+ * qts_exact_nodes - the points QTS_NQ_EXACT takes for an order-`order` quantity
+ * on paths with at most `width` unique features: ceil((width - order + 1) / 2),
+ * at least 1 (Thm 2: the order-s integrand has degree at most d - s, and n
+ * points integrate degree 2n - 1 exactly).  Returns 0 unless
+ * 1 <= width <= QTS_MAX_UNIQUE_FEATURES_PER_PATH and order >= 1.
+ */
+int32_t qts_exact_nodes(int32_t width, int32_t order);
 
 /* Thread-local description of the last error (never NULL). */
 const char *qts_last_error(void);

@@ -19,6 +19,9 @@ LIB_PATH = os.path.join(_HERE, "libqtreeshap.so")
 QTS_OK = 0
 QTS_FLAG_FP64 = 1
 QTS_DESCRIBE_PAIRS = 2
+# n_quad = EXACT_NODES: per path width w the fewest Gauss-Legendre points that
+# integrate an order-s quantity exactly, ceil((w - s + 1) / 2) (Thm 2)
+EXACT_NODES = 0
 STATUS_NAMES = {0: "QTS_OK", 1: "QTS_ERR_ARG", 2: "QTS_ERR_CUDA", 3: "QTS_ERR_OOM",
                 4: "QTS_ERR_UNSUPPORTED", 5: "QTS_ERR_TIMEOUT", 6: "QTS_ERR_DEVICE_CHECK"}
 
@@ -27,7 +30,7 @@ EXPORTS = ("qts_load_ensemble", "qts_load_ensemble_cat", "qts_update_params", "q
            "qts_shap_interactions",
            "qts_shap_interactions_noalloc", "qts_shap_interactions3", "qts_shap_interactions_order",
            "qts_shap_backward", "qts_batched_fwd_bwd", "qts_batched_autotune", "qts_get_batch_info", "qts_autotune", "qts_sync_status",
-           "qts_get_info", "qts_describe_ensemble", "qts_describe_paths", "qts_describe_alg1_program", "qts_selftest_wait_timeout", "qts_batched_kernel_count", "qts_batched_last_kernel_ms", "qts_gauss_legendre", "qts_last_error",
+           "qts_get_info", "qts_describe_ensemble", "qts_describe_paths", "qts_describe_alg1_program", "qts_selftest_wait_timeout", "qts_batched_kernel_count", "qts_batched_last_kernel_ms", "qts_gauss_legendre", "qts_exact_nodes", "qts_last_error",
            "qts_free")
 
 _lib = None
@@ -80,7 +83,7 @@ def lib():
         L.qts_shap_backward.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp, vp]
         L.qts_batched_fwd_bwd.argtypes = [i32, vp, i32, vp]
         L.qts_batched_autotune.argtypes = [i32, vp, i32, i64, vp, vp]
-        L.qts_get_batch_info.argtypes = [vp, vp, vp, vp]
+        L.qts_get_batch_info.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.qts_autotune.argtypes = [vp, vp, i64, i32, ctypes.c_char_p, vp]
         L.qts_sync_status.argtypes = [vp, vp]
         L.qts_selftest_wait_timeout.argtypes = [vp, vp]
@@ -88,6 +91,7 @@ def lib():
         L.qts_describe_ensemble.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, u32,
                                             ctypes.POINTER(QtsInfo)]
         L.qts_gauss_legendre.argtypes = [i32, vp, vp]
+        L.qts_exact_nodes.argtypes = [i32, i32]
         L.qts_describe_alg1_program.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp]
         L.qts_describe_paths.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp]
         L.qts_batched_kernel_count.argtypes = []
@@ -97,9 +101,10 @@ def lib():
         L.qts_free.argtypes = [vp]
         L.qts_free.restype = None
         for f in EXPORTS:
-            if f not in ("qts_last_error", "qts_free", "qts_batched_kernel_count"):
+            if f not in ("qts_last_error", "qts_free", "qts_batched_kernel_count", "qts_exact_nodes"):
                 getattr(L, f).restype = ctypes.c_int
         L.qts_batched_kernel_count.restype = ctypes.c_int32
+        L.qts_exact_nodes.restype = ctypes.c_int32
         _lib = L
     return _lib
 
@@ -126,6 +131,12 @@ def gauss_legendre(n: int):
     w = np.zeros(n)
     _check(lib().qts_gauss_legendre(n, t.ctypes.data, w.ctypes.data))
     return t, w
+
+
+def exact_nodes(width: int, order: int = 1) -> int:
+    """Points n_quad = EXACT_NODES takes on paths of `width` unique features
+    for an order-`order` quantity (0 for arguments out of range)."""
+    return int(lib().qts_exact_nodes(width, order))
 
 
 def _info_dict(i: QtsInfo) -> dict:
@@ -241,8 +252,13 @@ class Ensemble:
     def batch_info(self) -> dict:
         """Sizes of the tables the batched pass uses (sibling leaf pairs merged)."""
         n, su, npair = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-        _check(lib().qts_get_batch_info(self.handle, ctypes.byref(n), ctypes.byref(su), ctypes.byref(npair)))
-        return dict(n_paths=n.value, sum_unique=su.value, n_pair_paths=npair.value)
+        nb = ctypes.c_int32()
+        bw = (ctypes.c_int32 * 32)()
+        bp = (ctypes.c_int64 * 32)()
+        _check(lib().qts_get_batch_info(self.handle, ctypes.byref(n), ctypes.byref(su), ctypes.byref(npair),
+                                        ctypes.byref(nb), bw, bp))
+        return dict(n_paths=n.value, sum_unique=su.value, n_pair_paths=npair.value,
+                    buckets=[(int(bw[i]), int(bp[i])) for i in range(nb.value)])
 
     def sync_status(self, stream=None):
         _check(lib().qts_sync_status(self.handle, _stream(stream)))

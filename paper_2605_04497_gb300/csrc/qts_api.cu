@@ -210,8 +210,8 @@ qts_status check_call(qts_ensemble* e, const float* X, int64_t M, int32_t F, int
     if (M < 0) return fail(QTS_ERR_ARG, "M must be >= 0");
     if (M > 0 && !X) return fail(QTS_ERR_ARG, "X is NULL");
     if (M > ((int64_t)1 << 31)) return fail(QTS_ERR_UNSUPPORTED, "M above 2^31 samples");
-    if (n_quad < 1 || n_quad > QTS_MAX_QUAD)
-        return fail(QTS_ERR_ARG, "n_quad must be in [1, " + std::to_string(QTS_MAX_QUAD) + "]");
+    if (n_quad != QTS_NQ_EXACT && (n_quad < 1 || n_quad > QTS_MAX_QUAD))
+        return fail(QTS_ERR_ARG, "n_quad must be QTS_NQ_EXACT or in [1, " + std::to_string(QTS_MAX_QUAD) + "]");
     return QTS_OK;
 }
 
@@ -226,6 +226,11 @@ const char* qts_last_error(void) { return g_err.c_str(); }
 qts_status qts_gauss_legendre(int32_t n, double* t, double* w) {
     if (!t || !w || n < 1 || n > 64) return fail(QTS_ERR_ARG, "n must be in [1, 64] and t, w non-NULL");
     return gauss_legendre(n, t, w) ? QTS_OK : fail(QTS_ERR_ARG, "gauss_legendre failed");
+}
+
+int32_t qts_exact_nodes(int32_t width, int32_t order) {
+    if (width < 1 || width > QTS_MAX_UNIQUE_FEATURES_PER_PATH || order < 1) return 0;
+    return exact_nodes(width, order);
 }
 
 static qts_status load_impl(int32_t n_trees, const int64_t* off, const int32_t* left,
@@ -342,9 +347,6 @@ qts_status qts_shap_values(qts_ensemble* e, const float* X, int64_t M, int32_t F
     if (M == 0) return QTS_OK;
     if (!phi) return fail(QTS_ERR_ARG, "phi is NULL");
     cudaStream_t s = (cudaStream_t)stream;
-    QuadF qf;
-    QuadD qd;
-    if (!make_quad(n_quad, &qf, &qd)) return fail(QTS_ERR_ARG, "quadrature rule");
     // FP32 runs on the pair tables (built on the first call that needs them)
     const bool fp64 = (e->flags & QTS_FLAG_FP64) != 0;
     if (!fp64) {
@@ -355,6 +357,10 @@ qts_status qts_shap_values(qts_ensemble* e, const float* X, int64_t M, int32_t F
     cudaError_t ce = launch_phi_init(phi, M, F, P.bias, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "phi init launch");
     for (const Bucket& b : P.buckets) {
+        // the bucket's rule, padded to whole node pairs (QTS_NQ_EXACT: ceil(D/2) points)
+        QuadF qf;
+        QuadD qd;
+        if (!make_quad(nodes_for(n_quad, b.D, 1), &qf, &qd, 2)) return fail(QTS_ERR_ARG, "quadrature rule");
         ce = launch_fwd_bucket(e, b, X, M, F, qf, qd, phi, e->tune[b.D], s);
         if (ce != cudaSuccess) return cuda_fail(ce, "forward kernel launch");
     }

@@ -189,13 +189,20 @@ __device__ __forceinline__ bool batch_item(const SegDev& sg, const ReqDev& rq, i
                     else bwd_path_f32_pk<D, false, kPhiAtomic, GlobalCols, GlobalCols, true>(r, xr, gr, my, lane, q, gsl, gv);
                 }
             } else {
-                if (priv) {
-                    if (has_nan) fwd_path_f32<D, FWD_NP, true, GlobalCols, kPhiPrivate, true>(r, xr, my, lane, q);
-                    else fwd_path_f32<D, FWD_NP, false, GlobalCols, kPhiPrivate, true>(r, xr, my, lane, q);
-                } else {
-                    if (has_nan) fwd_path_f32<D, FWD_NP, true, GlobalCols, kPhiAtomic, true>(r, xr, my, lane, q);
-                    else fwd_path_f32<D, FWD_NP, false, GlobalCols, kPhiAtomic, true>(r, xr, my, lane, q);
-                }
+                auto fwd = [&](auto np) {
+                    constexpr int NP = decltype(np)::value;
+                    if (priv) {
+                        if (has_nan) fwd_path_f32<D, NP, true, GlobalCols, kPhiPrivate, true>(r, xr, my, lane, q);
+                        else fwd_path_f32<D, NP, false, GlobalCols, kPhiPrivate, true>(r, xr, my, lane, q);
+                    } else {
+                        if (has_nan) fwd_path_f32<D, NP, true, GlobalCols, kPhiAtomic, true>(r, xr, my, lane, q);
+                        else fwd_path_f32<D, NP, false, GlobalCols, kPhiAtomic, true>(r, xr, my, lane, q);
+                    }
+                };
+                // a rule of fewer than FWD_NP points (or not a multiple of it)
+                // runs node pairs
+                if (FWD_NP > 2 && q.n_pad % FWD_NP != 0) fwd(std::integral_constant<int, 2>{});
+                else fwd(std::integral_constant<int, FWD_NP>{});
             }
         },
         priv);
@@ -484,14 +491,16 @@ struct BatchOverride {
     int only_width;
 };
 
-static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, BatchPlan* plan,
+static qts_status build_plan(int n, const qts_request* reqs, int n_quad, BatchPlan* plan,
                              cudaStream_t cap, const BatchOverride* ov = nullptr) {
     struct SegHost {
         SegDev d;
         double cost;  // per item
         int cls;
         int64_t tile;  // floats of its phi region
-        int bin;       // tile-size bin: one launch per (class, bin)
+        int bin;       // tile-size bin: one launch per (class, bin, rule)
+        int nq;        // quadrature points of the bucket (QTS_NQ_EXACT: ceil(D/2))
+        int npad;      // ... padded to what its variant of the pass takes per register pass
     };
     std::vector<SegHost> segs;
     std::vector<ReqDev> rd(n);
@@ -531,7 +540,11 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
             s.d.req = r;
             s.d.priv = mode;
             s.d.pad = 0;
-            s.cost = (double)s.d.paths * b.D * (grad ? 12 : 4);
+            s.nq = nodes_for(n_quad, b.D, 1);
+            // the packed fused pass takes one node at a time, the others node pairs
+            const int pad = (grad && mode >= 2) ? 1 : 2;
+            s.npad = (s.nq + pad - 1) / pad * pad;
+            s.cost = (double)s.d.paths * b.D * (grad ? 12 : 4) * s.npad;
             s.cls = cls;
             // a launch sizes its shared memory for its widest tile, and whatever
             // shared memory a block does not take stays L1 (which serves the x and
@@ -542,18 +555,24 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
             segs.push_back(s);
         }
     }
-    // one launch per (kernel class, tile bin), heaviest items first within it
+    // one launch per (kernel class, tile bin, quadrature rule), heaviest items
+    // first within it
     std::stable_sort(segs.begin(), segs.end(), [](const SegHost& a, const SegHost& b) {
         if (a.cls != b.cls) return a.cls < b.cls;
         if (a.bin != b.bin) return a.bin < b.bin;
+        if (a.npad != b.npad) return a.npad > b.npad;
+        if (a.nq != b.nq) return a.nq > b.nq;
         return a.cost > b.cost;
     });
-    std::vector<int> cls_list;
+    std::vector<int> cls_list, cls_nq, cls_npad;
     std::vector<int64_t> cls_items, cls_first_seg, cls_tile;
     int64_t item = 0;
     for (size_t i = 0; i < segs.size(); ++i) {
-        if (cls_list.empty() || cls_list.back() != segs[i].cls || segs[i - 1].bin != segs[i].bin) {
+        if (cls_list.empty() || cls_list.back() != segs[i].cls || segs[i - 1].bin != segs[i].bin ||
+            segs[i - 1].nq != segs[i].nq || segs[i - 1].npad != segs[i].npad) {
             cls_list.push_back(segs[i].cls);
+            cls_nq.push_back(segs[i].nq);
+            cls_npad.push_back(segs[i].npad);
             cls_first_seg.push_back((int64_t)i);
             cls_items.push_back(0);
             cls_tile.push_back(0);
@@ -624,7 +643,10 @@ static qts_status build_plan(int n, const qts_request* reqs, const QuadF& q, Bat
         a.counter = d_cnt + c;
         a.tile_floats = std::max<int64_t>(cls_tile[c], kTileLd);
         a.sub = sub;
-        a.q = q;
+        if (!make_quad(cls_nq[c], &a.q, nullptr, cls_npad[c] == cls_nq[c] ? 1 : 2) || a.q.n_pad != cls_npad[c]) {
+            err = cudaErrorInvalidValue;
+            break;
+        }
         const size_t smem = batch_smem_bytes(a.tile_floats, sub, cls);
         int blocks = 0;
         if (cls == 8) err = launch_batch_class<8>(a, smem, cap, &blocks);
@@ -677,9 +699,8 @@ namespace qts {
 
 // Argument checks shared by the batched call and its tuner; grows every
 // request's workspace to what the batched launch needs.
-static qts_status check_batch(int32_t n, const qts_request* reqs, int32_t n_quad, QuadF* qf) {
+static qts_status check_batch(int32_t n, const qts_request* reqs, int32_t n_quad) {
     if (n < 1 || !reqs) return fail(QTS_ERR_ARG, "no requests");
-    if (!make_quad(n_quad, qf, nullptr)) return fail(QTS_ERR_ARG, "n_quad must be in [1, 32]");
     for (int r = 0; r < n; ++r) {
         const qts_request& R = reqs[r];
         qts_status st = check_call(R.ens, R.X, R.M, R.F, n_quad);
@@ -707,9 +728,8 @@ static qts_status check_batch(int32_t n, const qts_request* reqs, int32_t n_quad
 
 extern "C" qts_status qts_batched_fwd_bwd(int32_t n, const qts_request* reqs, int32_t n_quad,
                                           qts_stream_t stream) {
-    QuadF qf;
     {
-        const qts_status st = check_batch(n, reqs, n_quad, &qf);
+        const qts_status st = check_batch(n, reqs, n_quad);
         if (st != QTS_OK) return st;
     }
     std::vector<uint64_t> key;
@@ -744,7 +764,7 @@ extern "C" qts_status qts_batched_fwd_bwd(int32_t n, const qts_request* reqs, in
         if (ce != cudaSuccess) return cuda_fail(ce, "capture stream");
         auto* plan = new BatchPlan();
         plan->key = key;
-        qts_status st = build_plan(n, reqs, qf, plan, cap);
+        qts_status st = build_plan(n, reqs, n_quad, plan, cap);
         cudaStreamDestroy(cap);
         if (st != QTS_OK) {
             destroy_plan(plan);
@@ -771,10 +791,10 @@ namespace qts {
 
 // Device time of the persistent kernels of one plan built for `reqs` with the
 // override `ov` (second of two launches); the plan is destroyed afterwards.
-static qts_status time_plan(int n, const qts_request* reqs, const QuadF& qf, const BatchOverride& ov,
+static qts_status time_plan(int n, const qts_request* reqs, int n_quad, const BatchOverride& ov,
                             cudaStream_t cap, cudaStream_t st, float* ms) {
     auto* plan = new BatchPlan();
-    qts_status s = build_plan(n, reqs, qf, plan, cap, &ov);
+    qts_status s = build_plan(n, reqs, n_quad, plan, cap, &ov);
     cudaError_t ce = cudaSuccess;
     for (int k = 0; k < 2 && s == QTS_OK && ce == cudaSuccess; ++k) ce = cudaGraphLaunch(plan->exec, st);
     if (s == QTS_OK && ce == cudaSuccess) ce = cudaEventSynchronize(plan->ev1);
@@ -789,8 +809,7 @@ static qts_status time_plan(int n, const qts_request* reqs, const QuadF& qf, con
 
 extern "C" qts_status qts_batched_autotune(int32_t n, const qts_request* reqs, int32_t n_quad, int64_t max_samples,
                                            int32_t* chosen, qts_stream_t stream) {
-    QuadF qf;
-    qts_status st = check_batch(n, reqs, n_quad, &qf);
+    qts_status st = check_batch(n, reqs, n_quad);
     if (st != QTS_OK) return st;
     if (max_samples < 0) return fail(QTS_ERR_ARG, "max_samples must be >= 0");
     std::vector<qts_request> sub(reqs, reqs + n);
@@ -833,7 +852,7 @@ extern "C" qts_status qts_batched_autotune(int32_t n, const qts_request* reqs, i
                 ov.paths[D] = paths;
                 ov.mode[D] = packed[D] ? mode : 0;
                 float ms = 0.f;
-                st = time_plan(n, sub.data(), qf, ov, cap, (cudaStream_t)stream, &ms);
+                st = time_plan(n, sub.data(), n_quad, ov, cap, (cudaStream_t)stream, &ms);
                 if (st != QTS_OK) {
                     cudaStreamDestroy(cap);
                     return st;
@@ -865,7 +884,8 @@ extern "C" qts_status qts_batched_autotune(int32_t n, const qts_request* reqs, i
 }
 
 extern "C" qts_status qts_get_batch_info(qts_ensemble* e, int64_t* n_paths, int64_t* sum_unique,
-                                         int64_t* n_pair_paths) {
+                                         int64_t* n_pair_paths, int32_t* n_buckets, int32_t* bucket_width,
+                                         int64_t* bucket_paths) {
     if (!e) return fail(QTS_ERR_ARG, "ensemble handle is NULL");
     if (e->flags & QTS_FLAG_FP64) return fail(QTS_ERR_UNSUPPORTED, "batched calls use FP32 tables");
     const qts_status st = ensure_batch_tables(e);
@@ -873,6 +893,12 @@ extern "C" qts_status qts_get_batch_info(qts_ensemble* e, int64_t* n_paths, int6
     if (n_paths) *n_paths = e->bprep.n_paths;
     if (sum_unique) *sum_unique = e->bprep.sum_unique;
     if (n_pair_paths) *n_pair_paths = e->bprep.n_pair_paths;
+    const size_t nb = std::min<size_t>(e->bprep.buckets.size(), 32);
+    if (n_buckets) *n_buckets = (int32_t)nb;
+    for (size_t i = 0; i < nb; ++i) {
+        if (bucket_width) bucket_width[i] = e->bprep.buckets[i].D;
+        if (bucket_paths) bucket_paths[i] = e->bprep.buckets[i].n_paths;
+    }
     return QTS_OK;
 }
 

@@ -265,7 +265,7 @@ cudaError_t launch_bwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
     if (M <= 0 || b.n_paths == 0) return cudaSuccess;
     const bool fp64 = (e->flags & QTS_FLAG_FP64) != 0;
     QuadD qd;
-    make_quad(q.n, nullptr, &qd);
+    make_quad(q.n, nullptr, &qd, 2);
     BwdArgs a;
     // FP32: the pair tables (two adjoint sums per path), FP64: the per-leaf tables
     a.rec = fp64 ? (const void*)((const Rec64*)e->d_rec + b.rec_off)
@@ -294,7 +294,9 @@ cudaError_t launch_bwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
     const size_t smem = bwd_smem_bytes(F, a.sub, b.D, fp64, with_phi);
     if (smem > kSmemMax) return cudaErrorInvalidConfiguration;
     const int warps = std::max(1, std::min(8, tn.warps));
-    const int np = b.D <= 8 ? 4 : 2;
+    // nodes per register pass; it must divide the rule's padded node count
+    const int np = (b.D <= 8 && q.n_pad % 4 == 0) ? 4 : 2;
+    if (q.n_pad % 2 != 0) return cudaErrorInvalidValue;
     switch (b.D) {
 #define QTS_CASE(DD) \
     case DD: return launch_bwd_d<DD>(a, np, fp64, with_phi, warps, blocks, smem, st);
@@ -415,8 +417,6 @@ extern "C" qts_status qts_shap_backward(qts_ensemble* e, const float* X, int64_t
     if (!d_leaf || !d_z) return fail(QTS_ERR_ARG, "d_leaf and d_z must be non-NULL");
     if (M > 0 && !grad_phi) return fail(QTS_ERR_ARG, "grad_phi is NULL");
     cudaStream_t s = (cudaStream_t)stream;
-    QuadF qf;
-    if (!make_quad(n_quad, &qf, nullptr)) return fail(QTS_ERR_ARG, "quadrature rule");
     // FP32 runs on the pair tables (two sums per path), FP64 on the per-leaf tables
     const bool fp64 = (e->flags & QTS_FLAG_FP64) != 0;
     if (!fp64) {
@@ -435,6 +435,9 @@ extern "C" qts_status qts_shap_backward(qts_ensemble* e, const float* X, int64_t
     if (ce != cudaSuccess) return cuda_fail(ce, "workspace clear");
     if (M > 0) {
         for (const Bucket& b : P.buckets) {
+            // the bucket's rule, padded to whole node pairs (QTS_NQ_EXACT: ceil(D/2) points)
+            QuadF qf;
+            if (!make_quad(nodes_for(n_quad, b.D, 1), &qf, nullptr, 2)) return fail(QTS_ERR_ARG, "quadrature rule");
             ce = launch_bwd_bucket(e, b, X, grad_phi, M, F, qf, g_val, g_slot, nullptr, e->tune[b.D], s);
             if (ce != cudaSuccess) return cuda_fail(ce, "adjoint kernel launch");
         }

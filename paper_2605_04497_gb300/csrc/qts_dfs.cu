@@ -541,7 +541,8 @@ extern "C" qts_status qts_shap_values_alg1(qts_ensemble* e, const float* X, int6
     cudaStream_t s = (cudaStream_t)stream;
     QuadF qf;
     QuadD qd;
-    if (!make_quad(n_quad, &qf, &qd)) return fail(QTS_ERR_ARG, "quadrature rule");
+    // QTS_NQ_EXACT: exact for the ensemble's widest path (first order, Thm 2)
+    if (!make_quad(nodes_for(n_quad, e->prep.max_unique, 1), &qf, &qd)) return fail(QTS_ERR_ARG, "quadrature rule");
     cudaError_t ce = launch_phi_init(phi, M, F, e->prep.bias, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "phi init launch");
     const int levels = std::max(e->dfs_levels, 1);

@@ -296,9 +296,14 @@ cudaError_t launch_fwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const size_t smem = fwd_smem_bytes(F, a.sub, b.D, fp64, a.ntiles, a.gphi != 0);
     if (smem > kSmemMax) return cudaErrorInvalidConfiguration;
+    // nodes per register pass: the tuned count, halved until it divides the rule's
+    // padded node count (every smaller power of two then divides it too)
+    int np = std::max(2, tn.np);
+    while (np > 2 && q.n_pad % np != 0) np /= 2;
+    if (!fp64 && q.n_pad % 2 != 0) return cudaErrorInvalidValue;
     switch (b.D) {
 #define QTS_CASE(DD) \
-    case DD: return launch_fwd_d<DD>(a, tn.np, fp64, warps, blocks, smem, st);
+    case DD: return launch_fwd_d<DD>(a, np, fp64, warps, blocks, smem, st);
         QTS_CASE(1) QTS_CASE(2) QTS_CASE(3) QTS_CASE(4) QTS_CASE(5) QTS_CASE(6) QTS_CASE(7)
         QTS_CASE(8) QTS_CASE(9) QTS_CASE(10) QTS_CASE(11) QTS_CASE(12) QTS_CASE(13) QTS_CASE(14)
         QTS_CASE(15) QTS_CASE(16) QTS_CASE(20) QTS_CASE(24) QTS_CASE(28) QTS_CASE(32)

@@ -365,8 +365,9 @@ extern "C" qts_status qts_shap_interactions(qts_ensemble* e, const float* X, int
     if (e->prep.max_unique > 32)
         return fail(QTS_ERR_UNSUPPORTED, "interactions support paths of at most 32 unique features");
     cudaStream_t s = (cudaStream_t)stream;
-    QuadF qf;
-    if (!make_quad(n_quad, &qf, nullptr)) return fail(QTS_ERR_ARG, "quadrature rule");
+    QuadF qf;  // QTS_NQ_EXACT: exact for the ensemble's widest path (order 2, Thm 2)
+    if (!make_quad(nodes_for(n_quad, e->prep.max_unique, 2), &qf, nullptr))
+        return fail(QTS_ERR_ARG, "quadrature rule");
     const int64_t n_pairs = (int64_t)F * (F - 1) / 2;
     const size_t bytes = sizeof(double) * (size_t)((n_pairs + F) * M);
     st = ensure_workspace(e, bytes);
@@ -479,8 +480,9 @@ extern "C" qts_status qts_shap_interactions_noalloc(qts_ensemble* e, const float
                         " accumulator doubles; the fixed scratch holds " + std::to_string(kNoAllocDoubles) +
                         " (use qts_shap_interactions for larger calls)");
     cudaStream_t s = (cudaStream_t)stream;
-    QuadF qf;
-    if (!make_quad(n_quad, &qf, nullptr)) return fail(QTS_ERR_ARG, "quadrature rule");
+    QuadF qf;  // QTS_NQ_EXACT: exact for the ensemble's widest path (order 2, Thm 2)
+    if (!make_quad(nodes_for(n_quad, e->prep.max_unique, 2), &qf, nullptr))
+        return fail(QTS_ERR_ARG, "quadrature rule");
     void* scratch = nullptr;
     st = noalloc_scratch(&scratch);
     if (st != QTS_OK) return st;

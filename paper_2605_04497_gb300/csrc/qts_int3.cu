@@ -262,8 +262,9 @@ extern "C" qts_status qts_shap_interactions3(qts_ensemble* e, const float* X, in
     // writes the same compact layout
     if (M <= kFewRows) return qts_shap_interactions_order(e, X, M, F, 3, n_quad, sii3, stream);
     cudaStream_t s = (cudaStream_t)stream;
-    QuadF qf;
-    if (!make_quad(n_quad, &qf, nullptr)) return fail(QTS_ERR_ARG, "quadrature rule");
+    QuadF qf;  // QTS_NQ_EXACT: exact for the ensemble's widest path (order 3, Thm 2)
+    if (!make_quad(nodes_for(n_quad, e->prep.max_unique, 3), &qf, nullptr))
+        return fail(QTS_ERR_ARG, "quadrature rule");
     const int64_t n_tri = choose3(F);
     if (n_tri == 0) return QTS_OK;
     const size_t bytes = sizeof(double) * (size_t)(n_tri * M);

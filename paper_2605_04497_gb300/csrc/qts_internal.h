@@ -223,7 +223,20 @@ struct QuadD {
     double w[QTS_MAX_QUAD + 8];
     int n, n_pad;
 };
-bool make_quad(int n, QuadF* qf, QuadD* qd);
+// n nodes, padded with zero-weight nodes to a multiple of `pad` (the node
+// count of one register pass of the kernel that takes the rule)
+bool make_quad(int n, QuadF* qf, QuadD* qd, int pad = 8);
+
+// Points that integrate an order-s quantity exactly on paths of at most
+// `width` unique features: ceil((width - s + 1) / 2), at least 1 (Thm 2).
+inline int exact_nodes(int width, int order) {
+    const int deg = width - order;  // degree of the integrand
+    return deg < 1 ? 1 : deg / 2 + 1;
+}
+// The points an n_quad argument asks for on paths of `width` unique features.
+inline int nodes_for(int n_quad, int width, int order) {
+    return n_quad == QTS_NQ_EXACT ? exact_nodes(width, order) : n_quad;
+}
 
 // validate common call arguments
 qts_status check_call(qts_ensemble* e, const float* X, int64_t M, int32_t F, int32_t n_quad);

@@ -339,8 +339,9 @@ extern "C" qts_status qts_shap_interactions_order(qts_ensemble* e, const float* 
     if (n_sub > ((int64_t)1 << 40) / std::max<int64_t>(M, 1))
         return fail(QTS_ERR_UNSUPPORTED, "C(F, order) * M is too large for the FP64 accumulators");
     cudaStream_t s = (cudaStream_t)stream;
-    QuadF qf;
-    if (!make_quad(n_quad, &qf, nullptr)) return fail(QTS_ERR_ARG, "quadrature rule");
+    QuadF qf;  // QTS_NQ_EXACT: exact for the ensemble's widest path (this order, Thm 2)
+    if (!make_quad(nodes_for(n_quad, e->prep.max_unique, order), &qf, nullptr))
+        return fail(QTS_ERR_ARG, "quadrature rule");
     const size_t bytes = sizeof(double) * (size_t)(n_sub * M);
     st = ensure_workspace(e, bytes);
     if (st != QTS_OK) return st;

@@ -86,10 +86,22 @@ bool gauss_legendre(int n, double* t, double* w) {
     return true;
 }
 
-bool make_quad(int n, QuadF* qf, QuadD* qd) {
-    double t[64], w[64];
-    if (n < 1 || n > QTS_MAX_QUAD || !gauss_legendre(n, t, w)) return false;
-    int npad = (n + 7) / 8 * 8;
+bool make_quad(int n, QuadF* qf, QuadD* qd, int pad) {
+    // the rules for 1..QTS_MAX_QUAD points, computed once (calls choose one
+    // per bucket, so this runs on every launch)
+    struct Rules {
+        double t[QTS_MAX_QUAD + 1][QTS_MAX_QUAD], w[QTS_MAX_QUAD + 1][QTS_MAX_QUAD];
+        bool ok[QTS_MAX_QUAD + 1];
+    };
+    static const Rules* rules = [] {
+        Rules* r = new Rules();
+        for (int k = 1; k <= QTS_MAX_QUAD; ++k) r->ok[k] = gauss_legendre(k, r->t[k], r->w[k]);
+        return r;
+    }();
+    if (n < 1 || n > QTS_MAX_QUAD || pad < 1 || pad > 8 || !rules->ok[n]) return false;
+    const double* t = rules->t[n];
+    const double* w = rules->w[n];
+    int npad = (n + pad - 1) / pad * pad;
     for (int i = 0; i < QTS_MAX_QUAD + 8; ++i) {
         double ti = i < n ? t[i] : 0.5, wi = i < n ? w[i] : 0.0;
         if (qf) { qf->t[i] = (float)ti; qf->w[i] = (float)wi; }

@@ -129,8 +129,9 @@ def test_edge_sizes(qts):
     X0 = torch.zeros((0, 8), dtype=torch.float32, device="cuda")
     out = qts.shap_values(E, X0)
     assert out.shape == (0, 9)
-    with pytest.raises(qts.QtsError):
-        qts.shap_values(E, torch.zeros((4, 8), device="cuda"), n_quad=0)
+    for bad in (-1, 33):  # 0 is EXACT_NODES, 1..32 a fixed count
+        with pytest.raises(qts.QtsError):
+            qts.shap_values(E, torch.zeros((4, 8), device="cuda"), n_quad=bad)
     E.close()
 
 
