@@ -339,6 +339,9 @@ def run_ours(args, rank, world, local):
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         max_mhz = float(pk.get("sm_max_mhz", 2070.0))
         peak = fp32_peak_tops(sms, max_mhz)
+        # the same denominator measured: independent FMA chains at full occupancy
+        probe = {"ffma2_tops": qts.fp32_pipe_peak(True) / 1e12, "ffma_tops": qts.fp32_pipe_peak(False) / 1e12,
+                 "source": "qts_fp32_pipe_peak (CUDA events, fastest of 3 launches)"}
         achieved = alg_ops / (kms / 1e3) / 1e12
         arm = lambda t, kernels: {"value": U / (float(np.mean(t)) / 1e3), "unit": UNIT,
                                   "ms_per_step": float(np.mean(t)), "steps": len(t), "kernels": kernels,
@@ -364,6 +367,7 @@ def run_ours(args, rank, world, local):
                          "traffic_note": "ALU-bound: one-request captures read tens of MB per launch (0.01% of HBM "
                                          "bandwidth); not scaled to the batch",
                          "peak_basis": f"{sms} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (max SM clock)",
+                         "peak_measured": probe,
                          "algorithmic_ops_per_launch": alg_ops,
                          "ops_basis": "11 FP32-pipe ops per (sample, merged element of a root-to-leaf path, "
                                       "quadrature node)",

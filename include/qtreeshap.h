@@ -199,7 +199,12 @@ qts_status qts_shap_values_alg1(qts_ensemble *ens, const float *X, int64_t M, in
  *           [s][i][i] = phi_i - sum_{j != i} SII_ij / 2 (rows sum to phi_i),
  *           [s][F][F] = E[f], other entries of row/column F are 0.
  * Cross-tree accumulation is FP64 in the ensemble's workspace (device memory
- * of M * (F(F+1)/2) doubles, grown on demand with cudaMalloc).
+ * of M * (F(F+1)/2) doubles, grown on demand with cudaMalloc).  Runs on the
+ * sibling-pair tables of qts_shap_values (each pair's element is one more
+ * linear factor of every pair term; built by the first call that needs them,
+ * so that call must not be inside a stream capture).  n_quad as
+ * qts_shap_values; QTS_NQ_EXACT takes ceil((d - 1) / 2) points for the
+ * ensemble's widest path d.
  */
 qts_status qts_shap_interactions(qts_ensemble *ens, const float *X, int64_t M, int32_t F,
                                  int32_t n_quad, float *phi_ij, qts_stream_t stream);
@@ -255,7 +260,9 @@ qts_status qts_shap_interactions_order(qts_ensemble *ens, const float *X, int64_
  * handle - so calls that overlap on the GPU (different streams, threads or
  * ensembles) race and give wrong results: serialise all calls on a device
  * across the process, not per ensemble.  Arguments and output layout as
- * qts_shap_interactions.
+ * qts_shap_interactions; it runs on the per-leaf path tables (building the
+ * sibling-pair tables would allocate), so its sums match
+ * qts_shap_interactions' to rounding, not bit for bit.
  */
 qts_status qts_shap_interactions_noalloc(qts_ensemble *ens, const float *X, int64_t M, int32_t F,
                                          int32_t n_quad, float *phi_ij, qts_stream_t stream);
@@ -473,6 +480,17 @@ qts_status qts_gauss_legendre(int32_t n, double *t, double *w);
  * 1 <= width <= QTS_MAX_UNIQUE_FEATURES_PER_PATH and order >= 1.
  */
 int32_t qts_exact_nodes(int32_t width, int32_t order);
+
+/*
+ * qts_fp32_pipe_peak - measured FP32-pipe throughput of this device, the
+ * denominator of the FP32 kernels' roofline: every thread of 8 blocks per SM
+ * runs 16 independent FMA chains (packed != 0: 8 chains of f32x2 FMAs), timed
+ * with CUDA events (fastest of three launches after one warm-up, about 20 ms
+ * each).  lane_ops_per_s: FMAs per second, one per FP32 lane (an f32x2 FMA
+ * counts two).  Synchronous on `stream`.  QTS_ERR_ARG for a NULL output,
+ * QTS_ERR_CUDA if a launch fails.
+ */
+qts_status qts_fp32_pipe_peak(int32_t packed, double *lane_ops_per_s, qts_stream_t stream);
 
 /* Thread-local description of the last error (never NULL). */
 const char *qts_last_error(void);

@@ -30,7 +30,7 @@ EXPORTS = ("qts_load_ensemble", "qts_load_ensemble_cat", "qts_update_params", "q
            "qts_shap_interactions",
            "qts_shap_interactions_noalloc", "qts_shap_interactions3", "qts_shap_interactions_order",
            "qts_shap_backward", "qts_batched_fwd_bwd", "qts_batched_autotune", "qts_get_batch_info", "qts_autotune", "qts_sync_status",
-           "qts_get_info", "qts_describe_ensemble", "qts_describe_paths", "qts_describe_alg1_program", "qts_selftest_wait_timeout", "qts_batched_kernel_count", "qts_batched_last_kernel_ms", "qts_gauss_legendre", "qts_exact_nodes", "qts_last_error",
+           "qts_get_info", "qts_describe_ensemble", "qts_describe_paths", "qts_describe_alg1_program", "qts_selftest_wait_timeout", "qts_batched_kernel_count", "qts_batched_last_kernel_ms", "qts_gauss_legendre", "qts_exact_nodes", "qts_fp32_pipe_peak", "qts_last_error",
            "qts_free")
 
 _lib = None
@@ -92,6 +92,7 @@ def lib():
                                             ctypes.POINTER(QtsInfo)]
         L.qts_gauss_legendre.argtypes = [i32, vp, vp]
         L.qts_exact_nodes.argtypes = [i32, i32]
+        L.qts_fp32_pipe_peak.argtypes = [i32, vp, vp]
         L.qts_describe_alg1_program.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp]
         L.qts_describe_paths.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp]
         L.qts_batched_kernel_count.argtypes = []
@@ -131,6 +132,14 @@ def gauss_legendre(n: int):
     w = np.zeros(n)
     _check(lib().qts_gauss_legendre(n, t.ctypes.data, w.ctypes.data))
     return t, w
+
+
+def fp32_pipe_peak(packed: bool = True, stream=None) -> float:
+    """Measured FP32-pipe throughput in lane FMAs per second (an f32x2 FMA
+    counts two)."""
+    v = ctypes.c_double()
+    _check(lib().qts_fp32_pipe_peak(1 if packed else 0, ctypes.byref(v), _stream(stream)))
+    return v.value
 
 
 def exact_nodes(width: int, order: int = 1) -> int:

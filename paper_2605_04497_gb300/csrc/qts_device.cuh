@@ -258,4 +258,31 @@ __device__ __forceinline__ bool load_tiles_t(float* tile, const float* __restric
     return __syncthreads_or(nan_seen) != 0;
 }
 
+// ------------------------------------------------------- sibling pairs --
+//
+// Pair tables (FP32 forward, adjoint, batched pass, pairwise interactions)
+// hold sibling leaves A, B of a numerical split as one path with val = 1 whose
+// last element e (kPairElem) stands for both: for a sample x it gives
+// d = val_k - alpha for the leaf k the sample reaches (x in the element's
+// interval, then left of theta), -alpha if neither.  h is the path header
+// {1, val_A - alpha, val_B - alpha, bits of theta}.
+__device__ __forceinline__ void pair_sides(float x, const Rec32& e, const Rec32& h, bool* oa, bool* ob) {
+    bool in, left;
+    if (x != x) {
+        in = (e.bits & kNanOk) != 0;
+        left = (e.bits & kDefLeft) != 0;
+    } else {
+        in = x >= e.lo && x < e.hi;
+        left = x < __uint_as_float(h.bits);
+    }
+    *oa = in && left;
+    *ob = in && !left;
+}
+
+__device__ __forceinline__ float pair_d(float x, const Rec32& e, const Rec32& h) {
+    bool oa, ob;
+    pair_sides(x, e, h, &oa, &ob);
+    return oa ? h.lo : (ob ? h.hi : -e.z);
+}
+
 }  // namespace qts

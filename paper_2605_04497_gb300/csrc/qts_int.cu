@@ -65,8 +65,12 @@ __device__ __forceinline__ void int_path_f32(const Rec32* __restrict__ r, const 
                                              int64_t M, int lane, int F, const QuadF& q) {
     constexpr int K = NP / 2;
     const float val = r[0].z;
+    // a sibling pair (pair tables only): its element sits last, after the
+    // padding and out of feature order, with d = val_k - alpha per sample and
+    // val = 1 (the pair polynomial is one more linear factor of every term)
+    const bool pair = (r[D].bits & kPairElem) != 0;
     float dd[D], c1[D];
-    int nreal = D;  // elements before the padding (padding sorts last)
+    int nreal = D;  // sorted elements before the padding (padding sorts last)
 #pragma unroll
     for (int j = 0; j < D; ++j) {
         const Rec32 e = r[1 + j];
@@ -74,9 +78,11 @@ __device__ __forceinline__ void int_path_f32(const Rec32* __restrict__ r, const 
         const float x = xs[f * kTileLd + lane];
         const bool o = satisfies<HAS_NAN>(x, e.lo, e.hi, e.bits);
         dd[j] = (o ? 1.f : 0.f) - e.z;
+        if (j == D - 1 && pair) dd[j] = pair_d(x, e, r[0]);
         c1[j] = 0.f;
         if (f >= F && j < nreal) nreal = j;
     }
+    if (pair && nreal > D - 1) nreal = D - 1;
     const int npass = q.n_pad / NP;
     for (int pass = 0; pass < npass; ++pass) {
         float2 T[K], A[D][K], P[D][K], S[D][K];
@@ -109,10 +115,10 @@ __device__ __forceinline__ void int_path_f32(const Rec32* __restrict__ r, const 
             for (int k = 1; k < K; ++k) a1 = fma2(P[j][k], S[j][k], a1);
             c1[j] += a1.x + a1.y;
         }
-        // pairs i < j among the real elements
+        // pairs i < j among the sorted elements, then (i, pair element)
 #pragma unroll
         for (int i = 0; i < D - 1; ++i) {
-            if (i + 1 >= nreal) break;
+            if (i + (pair ? 0 : 1) >= nreal) break;
             const int fi = feat_of(r[1 + i].bits);
             const int64_t rowbase = tri_index(fi, fi + 1, F) - (fi + 1);  // + fj gives the index
             float2 R[K];
@@ -136,11 +142,27 @@ __device__ __forceinline__ void int_path_f32(const Rec32* __restrict__ r, const 
                     if (s < M && v != 0.f) atomicAdd(&acc_pair[idx * M + s], (double)v);
                 }
             }
+            if (pair) {
+                // R spans the elements between i and the pair element (padding
+                // factors are 1), and the pair element's suffix is 1
+                float2 acc = R[0];
+#pragma unroll
+                for (int k = 1; k < K; ++k) acc = add2(R[k], acc);
+                const float v = (acc.x + acc.y) * (dd[i] * dd[D - 1]);
+                const int fp = feat_of(r[D].bits);
+                const int64_t idx = fi < fp ? tri_index(fi, fp, F) : tri_index(fp, fi, F);
+                if constexpr (PAIR_SMEM) {
+                    atomicAdd(&pt[idx * kTileLd + lane], v);
+                } else {
+                    if (s < M && v != 0.f) atomicAdd(&acc_pair[idx * M + s], (double)v);
+                }
+            }
         }
     }
 #pragma unroll
     for (int j = 0; j < D; ++j)
-        if (j < nreal) atomicAdd(&ps[feat_of(r[1 + j].bits) * kTileLd + lane], dd[j] * c1[j]);
+        if (j < nreal || (pair && j == D - 1))
+            atomicAdd(&ps[feat_of(r[1 + j].bits) * kTileLd + lane], dd[j] * c1[j]);
 }
 
 template <int D, int NP, bool PAIR_SMEM>
@@ -302,23 +324,24 @@ __global__ void int_finalize_kernel(const double* __restrict__ acc_pair, const d
 
 static constexpr size_t kSmemBudget = 200 * 1024;
 
-cudaError_t launch_int_bucket(const qts_ensemble* e, const Bucket& b, const float* X, int64_t M, int F,
-                              const QuadF& q, double* acc_pair, double* acc_phi, cudaStream_t st) {
+cudaError_t launch_int_bucket(const qts_ensemble* e, const Bucket& b, bool pairs, const float* X, int64_t M,
+                              int F, const QuadF& q, double* acc_pair, double* acc_phi, cudaStream_t st) {
     if (M <= 0 || b.n_paths == 0) return cudaSuccess;
     IntArgs a;
-    a.rec = (const Rec32*)e->d_rec + b.rec_off;
+    // pairs: the sibling-pair tables (the bucket is one of e->bprep's)
+    a.rec = (pairs ? (const Rec32*)e->bdev.rec : (const Rec32*)e->d_rec) + b.rec_off;
     a.n_paths = b.n_paths;
     a.sub = b.D <= 16 ? 16 : 8;
     // wide inputs: stage fewer paths at a time until the block fits shared memory
     while (a.sub > 1 && int_smem_bytes(F, a.sub, b.D, false) > kSmemMax) a.sub /= 2;
+    a.group = M <= kFewRows ? (int)(32 / M) : 0;
     a.paths_per_block = std::max<int64_t>(a.sub, 512 / a.sub * a.sub);
     if (a.group) a.paths_per_block = std::max<int64_t>(a.paths_per_block, 4LL * 4 * a.group);
     a.n_tiles = (int)((M + 31) / 32);
-    a.group = M <= kFewRows ? (int)(32 / M) : 0;
     a.X = X;
     a.M = M;
     a.F = F;
-    a.cat = e->prep.has_cat ? 1 : 0;
+    a.cat = (pairs ? e->bprep.has_cat : e->prep.has_cat) ? 1 : 0;
     a.n_pairs = (int64_t)F * (F - 1) / 2;
     a.acc_pair = acc_pair;
     a.acc_phi = acc_phi;
@@ -368,6 +391,9 @@ extern "C" qts_status qts_shap_interactions(qts_ensemble* e, const float* X, int
     QuadF qf;  // QTS_NQ_EXACT: exact for the ensemble's widest path (order 2, Thm 2)
     if (!make_quad(nodes_for(n_quad, e->prep.max_unique, 2), &qf, nullptr))
         return fail(QTS_ERR_ARG, "quadrature rule");
+    // the sibling-pair tables (built on the first call that needs them)
+    st = ensure_batch_tables(e);
+    if (st != QTS_OK) return st;
     const int64_t n_pairs = (int64_t)F * (F - 1) / 2;
     const size_t bytes = sizeof(double) * (size_t)((n_pairs + F) * M);
     st = ensure_workspace(e, bytes);
@@ -376,11 +402,11 @@ extern "C" qts_status qts_shap_interactions(qts_ensemble* e, const float* X, int
     double* acc_phi = acc_pair + n_pairs * M;
     cudaError_t ce = cudaMemsetAsync(e->d_work, 0, bytes, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "workspace clear");
-    for (const Bucket& b : e->prep.buckets) {
-        ce = launch_int_bucket(e, b, X, M, F, qf, acc_pair, acc_phi, s);
+    for (const Bucket& b : e->bprep.buckets) {
+        ce = launch_int_bucket(e, b, true, X, M, F, qf, acc_pair, acc_phi, s);
         if (ce != cudaSuccess) return cuda_fail(ce, "interaction kernel launch");
     }
-    ce = launch_int_finalize(acc_pair, acc_phi, M, F, e->prep.bias, phi_ij, s);
+    ce = launch_int_finalize(acc_pair, acc_phi, M, F, e->bprep.bias, phi_ij, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "interaction finalize launch");
     return QTS_OK;
 }
@@ -492,7 +518,7 @@ extern "C" qts_status qts_shap_interactions_noalloc(qts_ensemble* e, const float
     cudaError_t ce = cudaMemsetAsync(scratch, 0, sizeof(double) * (size_t)need, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "scratch clear");
     for (const Bucket& b : e->prep.buckets) {
-        ce = launch_int_bucket(e, b, X, M, F, qf, acc_pair, acc_phi, s);
+        ce = launch_int_bucket(e, b, false, X, M, F, qf, acc_pair, acc_phi, s);
         if (ce != cudaSuccess) return cuda_fail(ce, "interaction kernel launch");
     }
     ce = launch_int_finalize(acc_pair, acc_phi, M, F, e->prep.bias, phi_ij, s);

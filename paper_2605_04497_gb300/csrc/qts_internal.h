@@ -249,7 +249,8 @@ cudaError_t launch_wait_selftest(int* status, cudaStream_t st);
 cudaError_t launch_fwd_bucket(const qts_ensemble* e, const Bucket& b, const float* X, int64_t M,
                               int F, const QuadF& q, const QuadD& qd, double* phi, const Tune& tn,
                               cudaStream_t st);
-cudaError_t launch_int_bucket(const qts_ensemble* e, const Bucket& b, const float* X, int64_t M,
+// pairs: b is a bucket of the sibling-pair tables (e->bprep), else of e->prep
+cudaError_t launch_int_bucket(const qts_ensemble* e, const Bucket& b, bool pairs, const float* X, int64_t M,
                               int F, const QuadF& q, double* acc_pair, double* acc_phi,
                               cudaStream_t st);
 cudaError_t launch_int_finalize(const double* acc_pair, const double* acc_phi, int64_t M, int F,

@@ -30,32 +30,6 @@ struct GlobalCols {  // transposed global copy [feature][ld]; this lane's sample
     __device__ __forceinline__ float operator()(int f) const { return __ldg(t + (int64_t)f * ld + s); }
 };
 
-// ------------------------------------------------------- sibling pairs --
-//
-// Pair tables (batched pass) hold sibling leaves A, B of a numerical split as
-// one path with val = 1 whose last element e (kPairElem) stands for both: for a
-// sample x it gives d = val_k - alpha for the leaf k the sample reaches (x in
-// the element's interval, then left of theta), -alpha if neither.  h is the
-// path header {1, val_A - alpha, val_B - alpha, bits of theta}.
-__device__ __forceinline__ void pair_sides(float x, const Rec32& e, const Rec32& h, bool* oa, bool* ob) {
-    bool in, left;
-    if (x != x) {
-        in = (e.bits & kNanOk) != 0;
-        left = (e.bits & kDefLeft) != 0;
-    } else {
-        in = x >= e.lo && x < e.hi;
-        left = x < __uint_as_float(h.bits);
-    }
-    *oa = in && left;
-    *ob = in && !left;
-}
-
-__device__ __forceinline__ float pair_d(float x, const Rec32& e, const Rec32& h) {
-    bool oa, ob;
-    pair_sides(x, e, h, &oa, &ob);
-    return oa ? h.lo : (ob ? h.hi : -e.z);
-}
-
 // The two extra sums of a pair path's adjoint.  With Q = acc2 - g acc1 the
 // pair element's z-gradient at val = 1 and K = acc3 - acc2 + g acc1 (acc3 =
 // sum_m w_m U_m, the part of acc2 without the (1 - t_m) factor), per sample

@@ -4,6 +4,8 @@ FP64 oracle (exact Bernstein integration of Thm 1 with |S| = 2).
 Per sample, max over the (F+1)^2 matrix of |gpu - oracle| divided by
 max(|f(x)|, max_i |phi_i|) must be <= 1e-5 (FP32 output, FP64 accumulation).
 """
+import itertools
+
 import numpy as np
 import pytest
 
@@ -89,3 +91,34 @@ def test_pairs_depth6_full_size_sampled_rows(qts):
     got = gpu_int(qts, w.ens, w.X)
     rows = np.r_[0:6, 1000:1004, 1994:2000]
     check(got[rows], w.ens, w.X[rows])
+
+
+def test_sibling_pair_paths(qts):
+    """The call runs on the tables where each pair of sibling leaves of a
+    numerical split is one path whose last element (out of feature order, after
+    the padding) stands for both leaves: stumps (paths with only that element),
+    the split feature repeated above, missing values with either default
+    direction, and the any-order kernel (per-leaf tables) as a second
+    reference."""
+    import torch
+
+    stumps = tiny_ensemble(1401, n_trees=9, depth=1, F=4, n_train=500)
+    X = synth.normal(1401, 1, (37, 4))
+    check(gpu_int(qts, stumps, X), stumps, X)
+    rep = tiny_ensemble(1402, n_trees=8, depth=10, F=4, n_train=4000)
+    X = synth.normal(1402, 1, (41, 4))
+    X[::3, 1] = np.nan
+    check(gpu_int(qts, rep, X), rep, X)
+    flipped = rep.copy()
+    flipped.default_left = 1 - flipped.default_left
+    check(gpu_int(qts, flipped, X), flipped, X)
+    E = qts.Ensemble.from_arrays(rep)
+    assert E.batch_info()["n_pair_paths"] > 0
+    Xd = torch.from_numpy(np.ascontiguousarray(X, np.float32)).cuda()
+    pairs = qts.shap_interactions(E, Xd).cpu().numpy().astype(np.float64)
+    leaves = qts.shap_interactions_order(E, Xd, 2).cpu().numpy().astype(np.float64)
+    E.sync_status()
+    E.close()
+    sii = np.stack([2.0 * pairs[:, a, b] for a, b in itertools.combinations(range(4), 2)], axis=1)
+    scale = np.abs(pairs).reshape(len(X), -1).max(1)[:, None]
+    assert (np.abs(sii - leaves) / scale).max() <= 2 * TOL32
