@@ -357,8 +357,9 @@ def run_ours(args, rank, world, local):
                        "n_quad": N_QUAD, "l2": "flushed between steps (256 MB write)",
                        "accumulation": "f64 across path chunks", "parallelism": "replicas" if world > 1 else "single",
                        "autotune": {"seconds": round(tune_s, 1), "samples_per_request": args.tune_samples,
-                                    "choices": {str(D): {"paths_per_item": p, "sample_mapping": m}
-                                                for D, (p, m) in sorted(tuned.items())}}},
+                                    "choices": {str(D): {"paths_per_item": p, "sample_mapping": m,
+                                                         "blocks_per_sm": o or "all that fit"}
+                                                for D, (p, m, o) in sorted(tuned.items())}}},
             "roofline": {"bound": "alu",
                          "kernel": "batch_kernel<8>, <12>, <16> (persistent fused forward + adjoint, one launch per register class)",
                          "achieved": achieved, "peak": peak, "unit": "Tops/s (FP32 pipe lane-ops)",

@@ -319,16 +319,20 @@ qts_status qts_batched_fwd_bwd(int32_t n_requests, const qts_request *reqs, int3
  * four and eight times the default, at most 4,096) and, where the fused pass
  * packs two samples per lane,
  * the sample mapping (each warp its own 64 samples, or the block's warps sharing
- * 64 samples and splitting the paths), and keeps the fastest.  The choices are
- * stored in each request's ensemble and used by later batched calls that
- * include it (their cached graphs are rebuilt).
+ * 64 samples and splitting the paths), and keeps the fastest.  Then, for the
+ * register classes of widths 1-6 and 7-10 (four and three blocks per SM), it
+ * times the class's launch with all blocks that fit and with one fewer, which
+ * leaves more of the SM's shared memory to L1, and keeps the faster.  The
+ * choices are stored in each request's ensemble and used by later batched
+ * calls that include it (their cached graphs are rebuilt).
  *   reqs, n, n_quad  as qts_batched_fwd_bwd; the requests' outputs are
  *                    overwritten with partial results
  *   max_samples      time on the first min(M, max_samples) samples of each
  *                    request (0: all)
- *   chosen           host, 2 * (QTS_MAX_UNIQUE_FEATURES_PER_PATH + 1) int32 or
- *                    NULL: for width D, [2D] paths per item, [2D + 1] mapping
- *                    (2 or 3, 0 where not packed); 0, 0 for untuned widths
+ *   chosen           host, 3 * (QTS_MAX_UNIQUE_FEATURES_PER_PATH + 1) int32 or
+ *                    NULL: for width D, [3D] paths per item, [3D + 1] mapping
+ *                    (2 or 3, 0 where not packed), [3D + 2] blocks per SM of
+ *                    its class (0: all that fit); 0 for untuned widths
  * Synchronous on `stream`.  Errors as qts_batched_fwd_bwd.
  */
 qts_status qts_batched_autotune(int32_t n_requests, const qts_request *reqs, int32_t n_quad,

@@ -440,12 +440,14 @@ def batched_fwd_bwd(reqs, n_quad: int = 8, stream=None):
 
 def batched_autotune(reqs, n_quad: int = 8, max_samples: int = 1024, stream=None) -> dict:
     """Tune the batched launch for these requests (see qts_batched_autotune);
-    returns {width: (paths per item, sample mapping)} for the tuned widths."""
+    returns {width: (paths per item, sample mapping, blocks per SM or 0)} for
+    the tuned widths."""
     n = 65  # QTS_MAX_UNIQUE_FEATURES_PER_PATH + 1
-    chosen = np.zeros(2 * n, dtype=np.int32)
+    chosen = np.zeros(3 * n, dtype=np.int32)
     _check(lib().qts_batched_autotune(len(reqs), ctypes.cast(reqs, ctypes.c_void_p), n_quad, max_samples,
                                       chosen.ctypes.data, _stream(stream)))
-    return {D: (int(chosen[2 * D]), int(chosen[2 * D + 1])) for D in range(n) if chosen[2 * D] > 0}
+    return {D: (int(chosen[3 * D]), int(chosen[3 * D + 1]), int(chosen[3 * D + 2]))
+            for D in range(n) if chosen[3 * D] > 0}
 
 
 def batched_last_kernel_ms() -> float:

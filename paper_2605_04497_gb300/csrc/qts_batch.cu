@@ -96,7 +96,7 @@ struct BatchNP {
 };
 
 template <int C>
-cudaError_t launch_batch_class(const BatchArgs& a, size_t smem, cudaStream_t st, int* blocks_out);
+cudaError_t launch_batch_class(const BatchArgs& a, size_t smem, cudaStream_t st, int* blocks_out, int occ = 0);
 
 #if QTS_DEVICE_PARTS
 
@@ -308,14 +308,16 @@ __global__ void __launch_bounds__(128, DCLASS == 8 ? 4 : (DCLASS == 12 ? 3 : (DC
     }
 }
 
+// occ > 0: at most occ blocks per SM (the persistent grid is occ x SMs blocks)
 template <int C>
-cudaError_t launch_batch_class(const BatchArgs& a, size_t smem, cudaStream_t st, int* blocks_out) {
+cudaError_t launch_batch_class(const BatchArgs& a, size_t smem, cudaStream_t st, int* blocks_out, int occ) {
     auto k = batch_kernel<C>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, smem);
     if (e != cudaSuccess) return e;
+    if (occ > 0) per_sm = std::min(per_sm, occ);
     const int blocks = std::max(1, per_sm) * num_sms();
     *blocks_out = blocks;
     k<<<blocks, 128, smem, st>>>(a);
@@ -323,7 +325,7 @@ cudaError_t launch_batch_class(const BatchArgs& a, size_t smem, cudaStream_t st,
 }
 
 #define QTS_INST(C) \
-    template cudaError_t launch_batch_class<C>(const BatchArgs&, size_t, cudaStream_t, int*);
+    template cudaError_t launch_batch_class<C>(const BatchArgs&, size_t, cudaStream_t, int*, int);
 #if QTS_IN_PART(1)
 QTS_INST(8)
 #endif
@@ -488,7 +490,9 @@ constexpr int kPrivRows = 64;
 struct BatchOverride {
     int paths[kMaxD + 1];
     int mode[kMaxD + 1];
+    int occ[kMaxD + 1];  // blocks per SM of the width's class (0: the tuned or full count)
     int only_width;
+    int only_class;      // > 0: only the widths of this register class
 };
 
 static qts_status build_plan(int n, const qts_request* reqs, int n_quad, BatchPlan* plan,
@@ -499,6 +503,7 @@ static qts_status build_plan(int n, const qts_request* reqs, int n_quad, BatchPl
         int cls;
         int64_t tile;  // floats of its phi region
         int bin;       // tile-size bin: one launch per (class, bin, rule)
+        int occ;       // blocks per SM of its class launch (0: as many as fit)
         int nq;        // quadrature points of the bucket (QTS_NQ_EXACT: ceil(D/2))
         int npad;      // ... padded to what its variant of the pass takes per register pass
     };
@@ -519,6 +524,7 @@ static qts_status build_plan(int n, const qts_request* reqs, int n_quad, BatchPl
         for (const Bucket& b : e->bprep.buckets) {
             if (ov && ov->only_width > 0 && b.D != ov->only_width) continue;
             const int cls = batch_class(b.D);
+            if (ov && ov->only_class > 0 && cls != ov->only_class) continue;
             const Tune& tn = e->tune[b.D];
             int mode = R.F + 1 <= kPrivRows ? 1 : 0;
             if (grad && pair_width(b.D) &&
@@ -540,6 +546,7 @@ static qts_status build_plan(int n, const qts_request* reqs, int n_quad, BatchPl
             s.d.req = r;
             s.d.priv = mode;
             s.d.pad = 0;
+            s.occ = ov && ov->occ[b.D] ? ov->occ[b.D] : tn.bt_occ;
             s.nq = nodes_for(n_quad, b.D, 1);
             // the packed fused pass takes one node at a time, the others node pairs
             const int pad = (grad && mode >= 2) ? 1 : 2;
@@ -564,7 +571,7 @@ static qts_status build_plan(int n, const qts_request* reqs, int n_quad, BatchPl
         if (a.nq != b.nq) return a.nq > b.nq;
         return a.cost > b.cost;
     });
-    std::vector<int> cls_list, cls_nq, cls_npad;
+    std::vector<int> cls_list, cls_nq, cls_npad, cls_occ;
     std::vector<int64_t> cls_items, cls_first_seg, cls_tile;
     int64_t item = 0;
     for (size_t i = 0; i < segs.size(); ++i) {
@@ -573,12 +580,15 @@ static qts_status build_plan(int n, const qts_request* reqs, int n_quad, BatchPl
             cls_list.push_back(segs[i].cls);
             cls_nq.push_back(segs[i].nq);
             cls_npad.push_back(segs[i].npad);
+            cls_occ.push_back(0);
             cls_first_seg.push_back((int64_t)i);
             cls_items.push_back(0);
             cls_tile.push_back(0);
             item = 0;
         }
         cls_tile.back() = std::max(cls_tile.back(), segs[i].tile);
+        // a launch takes the smallest cap of its widths
+        if (segs[i].occ > 0 && (cls_occ.back() == 0 || segs[i].occ < cls_occ.back())) cls_occ.back() = segs[i].occ;
         segs[i].d.item_begin = item;
         const int64_t chunks = (segs[i].d.n_paths + segs[i].d.paths - 1) / segs[i].d.paths;
         item += chunks * segs[i].d.n_tiles;
@@ -649,14 +659,14 @@ static qts_status build_plan(int n, const qts_request* reqs, int n_quad, BatchPl
         }
         const size_t smem = batch_smem_bytes(a.tile_floats, sub, cls);
         int blocks = 0;
-        if (cls == 8) err = launch_batch_class<8>(a, smem, cap, &blocks);
-        else if (cls == 12) err = launch_batch_class<12>(a, smem, cap, &blocks);
-        else if (cls == 16) err = launch_batch_class<16>(a, smem, cap, &blocks);
-        else if (cls == 32) err = launch_batch_class<32>(a, smem, cap, &blocks);
-        else if (cls == 40) err = launch_batch_class<40>(a, smem, cap, &blocks);
-        else if (cls == 48) err = launch_batch_class<48>(a, smem, cap, &blocks);
-        else if (cls == 56) err = launch_batch_class<56>(a, smem, cap, &blocks);
-        else err = launch_batch_class<64>(a, smem, cap, &blocks);
+        if (cls == 8) err = launch_batch_class<8>(a, smem, cap, &blocks, cls_occ[c]);
+        else if (cls == 12) err = launch_batch_class<12>(a, smem, cap, &blocks, cls_occ[c]);
+        else if (cls == 16) err = launch_batch_class<16>(a, smem, cap, &blocks, cls_occ[c]);
+        else if (cls == 32) err = launch_batch_class<32>(a, smem, cap, &blocks, cls_occ[c]);
+        else if (cls == 40) err = launch_batch_class<40>(a, smem, cap, &blocks, cls_occ[c]);
+        else if (cls == 48) err = launch_batch_class<48>(a, smem, cap, &blocks, cls_occ[c]);
+        else if (cls == 56) err = launch_batch_class<56>(a, smem, cap, &blocks, cls_occ[c]);
+        else err = launch_batch_class<64>(a, smem, cap, &blocks, cls_occ[c]);
         ++kernels;
     }
     if (err == cudaSuccess) err = cudaEventRecordWithFlags(plan->ev1, cap, cudaEventRecordExternal);
@@ -865,6 +875,36 @@ extern "C" qts_status qts_batched_autotune(int32_t n, const qts_request* reqs, i
             }
         }
     }
+    // blocks per SM of the two register classes that fit three or more: all
+    // that fit, or one fewer, which leaves the SM's shared memory more L1 for
+    // the x and grad_phi reads; timed over the class's widths with the choices
+    // above
+    std::vector<int> best_occ(kMaxD + 1, 0);
+    for (int cls : {8, 12}) {
+        bool any = false;
+        for (int D : widths) any = any || batch_class(D) == cls;
+        if (!any) continue;
+        const int full = cls == 8 ? 4 : 3;
+        BatchOverride ov;
+        std::memset(&ov, 0, sizeof(ov));
+        ov.only_class = cls;
+        for (int D = 1; D <= kMaxD; ++D) {
+            ov.paths[D] = best_paths[D];
+            ov.mode[D] = best_mode[D];
+        }
+        float t[2] = {0.f, 0.f};
+        for (int k = 0; k < 2; ++k) {
+            for (int D = 1; D <= kMaxD; ++D) ov.occ[D] = (k == 1 && batch_class(D) == cls) ? full - 1 : 0;
+            st = time_plan(n, sub.data(), n_quad, ov, cap, (cudaStream_t)stream, &t[k]);
+            if (st != QTS_OK) {
+                cudaStreamDestroy(cap);
+                return st;
+            }
+        }
+        if (t[1] < t[0])
+            for (int D = 1; D <= kMaxD; ++D)
+                if (batch_class(D) == cls) best_occ[D] = full - 1;
+    }
     cudaStreamDestroy(cap);
     for (int r = 0; r < n; ++r) {
         qts_ensemble* e = reqs[r].ens;
@@ -872,13 +912,15 @@ extern "C" qts_status qts_batched_autotune(int32_t n, const qts_request* reqs, i
             e->tune[D].bt_paths = best_paths[D];
             e->tune[D].bt_mode = best_mode[D];
         }
+        for (int D = 1; D <= kMaxD; ++D) e->tune[D].bt_occ = best_occ[D];
         ++e->tune_gen;
         batch_forget(e);
     }
     if (chosen)
         for (int D = 0; D <= kMaxD; ++D) {
-            chosen[2 * D] = best_paths[D];
-            chosen[2 * D + 1] = best_mode[D];
+            chosen[3 * D] = best_paths[D];
+            chosen[3 * D + 1] = best_mode[D];
+            chosen[3 * D + 2] = best_occ[D];
         }
     return QTS_OK;
 }

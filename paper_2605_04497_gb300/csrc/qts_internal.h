@@ -146,6 +146,8 @@ struct Tune {
     int bt_paths = 0;     // paths per work item of the persistent batched kernel
     int bt_mode = 0;      // sample mapping of the packed fused pass: 2 (64 samples
                           // per warp) or 3 (64 samples shared by the block's warps)
+    int bt_occ = 0;       // blocks per SM of the width's register class (0: as many as
+                          // fit; fewer leave more of the SM's shared memory to L1)
 };
 
 }  // namespace qts

@@ -145,6 +145,7 @@ extern "C" qts_status qts_autotune(qts_ensemble* e, const float* X, int64_t M, i
             e->tune[D] = it->second;
             e->tune[D].bt_paths = keep.bt_paths;
             e->tune[D].bt_mode = keep.bt_mode;
+            e->tune[D].bt_occ = keep.bt_occ;
             continue;
         }
         Tune best = e->tune[D];

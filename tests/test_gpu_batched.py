@@ -158,8 +158,8 @@ def test_batched_autotune_keeps_results(qts):
     reqs = qts.make_requests(items)
     chosen = qts.batched_autotune(reqs, 8, max_samples=64)
     assert chosen, "some width must carry 1% of the work"
-    for D, (paths, mode) in chosen.items():
-        assert paths >= 32 and mode in (0, 2, 3), (D, paths, mode)
+    for D, (paths, mode, occ) in chosen.items():
+        assert paths >= 32 and mode in (0, 2, 3) and occ in (0, 2, 3), (D, paths, mode, occ)
     qts.batched_fwd_bwd(reqs)
     torch.cuda.synchronize()
     for w, it in zip(works, items):
