@@ -187,6 +187,7 @@ qts_status qts_shap_values(qts_ensemble *ens, const float *X, int64_t M, int32_t
  * after qts_update_params) builds the traversal program on the host and uploads
  * it with cudaMalloc and a synchronous cudaMemcpy, so it must not be the first
  * call inside a stream capture; later calls only enqueue on `stream`.
+ * QTS_NQ_EXACT takes ceil(d / 2) points for the ensemble's widest path d.
  */
 qts_status qts_shap_values_alg1(qts_ensemble *ens, const float *X, int64_t M, int32_t F,
                                 int32_t n_quad, double *phi, qts_stream_t stream);
@@ -305,7 +306,10 @@ typedef struct qts_request {
  * the adjoint's).  The whole call (initialisation, persistent kernel, adjoint
  * epilogue) is captured once into a CUDA graph keyed by the request set and
  * replayed on later calls with the same requests.  Each ensemble may appear in
- * at most one request of a call.  FP32 ensembles only.
+ * at most one request of a call.  FP32 ensembles only.  n_quad as
+ * qts_shap_values; with QTS_NQ_EXACT every bucket takes ceil(D / 2) points for
+ * its width D and the graph holds one persistent launch per (register class,
+ * accumulator-tile size, rule).
  */
 qts_status qts_batched_fwd_bwd(int32_t n_requests, const qts_request *reqs, int32_t n_quad,
                                qts_stream_t stream);
