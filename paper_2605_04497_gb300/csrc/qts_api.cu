@@ -42,6 +42,9 @@ static Tune default_tune(int D) {
     t.paths = D <= 8 ? 512 : (D <= 16 ? 256 : 128);
     t.np = D <= 8 ? 8 : (D <= 24 ? 4 : 2);
     t.bpaths = 128;
+    // forward: up to width 8 the block's warps share a sample tile and split
+    // the paths (one phi tile each); wider paths give each warp its own samples
+    t.priv = D <= 8 ? 2 : 1;
     return t;
 }
 

@@ -38,6 +38,9 @@ struct FwdArgs {
                         // memory), contributions go straight to phi with FP64 atomics
     int group;          // few samples (M <= 16): lanes are (path, sample) pairs, a warp
                         // takes `group` = 32 / M paths at a time (FP32 only); 0 otherwise
+    int nphi;           // phi tiles: ntiles, or (FP32, ntiles = 1) one per warp, when the
+                        // warps share a sample tile, split the paths and each add into
+                        // its own phi tile (no atomics; summed at the flush)
     QuadF q;
     QuadD qd;
 };
@@ -51,16 +54,16 @@ cudaError_t launch_fwd_d(const FwdArgs& a, int np, bool fp64, int warps, int64_t
 // --------------------------------------------------------------- kernel ---
 
 template <typename Rec, typename Acc>
-__device__ __forceinline__ size_t fwd_smem_layout(int F, int sub, int D, int ntiles, bool gphi, float** xs,
-                                                  Acc** ps, Rec** stage0, Rec** stage1, uint64_t** bars,
-                                                  unsigned char* base) {
+__device__ __forceinline__ size_t fwd_smem_layout(int F, int sub, int D, int ntiles, int nphi, bool gphi,
+                                                  float** xs, Acc** ps, Rec** stage0, Rec** stage1,
+                                                  uint64_t** bars, unsigned char* base) {
     const int rows = F + 1;
     size_t off = 0;
     *xs = (float*)(base + off);
     off += (size_t)ntiles * rows * kTileLd * sizeof(float);
     off = (off + 15) & ~(size_t)15;
     *ps = (Acc*)(base + off);
-    if (!gphi) off += (size_t)ntiles * rows * kTileLd * sizeof(Acc);
+    if (!gphi) off += (size_t)nphi * rows * kTileLd * sizeof(Acc);
     off = (off + 15) & ~(size_t)15;
     *stage0 = (Rec*)(base + off);
     off += (size_t)sub * (D + 1) * sizeof(Rec);
@@ -81,13 +84,14 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
     Acc* ps;
     Rec *st0, *st1;
     uint64_t* bars;
-    fwd_smem_layout<Rec, Acc>(a.F, a.sub, D, a.ntiles, a.gphi != 0, &xs, &ps, &st0, &st1, &bars, smem);
+    fwd_smem_layout<Rec, Acc>(a.F, a.sub, D, a.ntiles, a.nphi, a.gphi != 0, &xs, &ps, &st0, &st1, &bars, smem);
     __shared__ int s_flag;
     __shared__ uint32_t s_phase[2];
 
     const int F = a.F;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool priv = a.ntiles > 1;
+    const bool priv = a.ntiles > 1;   // each warp its own samples and phi tile
+    const bool own = a.nphi > 1;      // each warp its own phi tile (priv, or split paths)
     const int stride = (F + 1) * kTileLd;
     const int group = (int)(blockIdx.x % (unsigned)a.n_tiles);
     const int64_t chunk = blockIdx.x / (unsigned)a.n_tiles;
@@ -95,7 +99,7 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
     const int64_t p0 = chunk * a.paths_per_block;
     const int64_t p1 = imin64(p0 + a.paths_per_block, a.n_paths);
     float* my_xs = priv ? xs + warp * stride : xs;
-    Acc* my_ps = priv ? ps + warp * stride : ps;
+    Acc* my_ps = own ? ps + warp * stride : ps;
     const int64_t sw = priv ? s0 + 32 * warp : s0;
 
     if (threadIdx.x == 0) {
@@ -105,7 +109,7 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
         s_phase[0] = s_phase[1] = 0;
     }
     if (!a.gphi)
-        for (int idx = threadIdx.x; idx < a.ntiles * stride; idx += blockDim.x) ps[idx] = (Acc)0;
+        for (int idx = threadIdx.x; idx < a.nphi * stride; idx += blockDim.x) ps[idx] = (Acc)0;
     // sample tiles (row = feature, column = sample) plus a zero row F for padding
     const bool has_nan = load_tiles_t(xs, a.X, s0, a.M, F, F, 1, a.ntiles, stride) || a.cat != 0;
 
@@ -141,7 +145,7 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
                 }
             } else {
                 const SmemCols xr{my_xs, lane};
-                if (priv) {
+                if (own) {
                     if (has_nan) fwd_path_f32<D, NP, true, SmemCols, kPhiPrivate, true>(r, xr, my_ps, lane, a.q);
                     else fwd_path_f32<D, NP, false, SmemCols, kPhiPrivate, true>(r, xr, my_ps, lane, a.q);
                 } else {
@@ -160,6 +164,16 @@ __global__ void __launch_bounds__(256) fwd_kernel(FwdArgs a) {
             if (sw + s < a.M) {
                 const Acc v = my_ps[f * kTileLd + s];
                 if (v != (Acc)0) atomicAdd(&a.phi[(sw + s) * (F + 1) + f], (double)v);
+            }
+        }
+    } else if (own) {
+        // stream_paths ended on a block barrier: every warp's tile is complete
+        for (int idx = threadIdx.x; idx < nflush; idx += blockDim.x) {
+            const int s = idx / F, f = idx - s * F;
+            if (s0 + s < a.M) {
+                Acc v = (Acc)0;
+                for (int w = 0; w < a.nphi; ++w) v += ps[w * stride + f * kTileLd + s];
+                if (v != (Acc)0) atomicAdd(&a.phi[(s0 + s) * (F + 1) + f], (double)v);
             }
         }
     } else {
@@ -244,11 +258,11 @@ cudaError_t launch_phi_init(double* phi, int64_t M, int F, double bias, cudaStre
     return cudaGetLastError();
 }
 
-size_t fwd_smem_bytes(int F, int sub, int D, bool fp64, int ntiles, bool gphi = false) {
+size_t fwd_smem_bytes(int F, int sub, int D, bool fp64, int ntiles, bool gphi = false, int nphi = 0) {
     const size_t rows = F + 1;
     size_t off = ntiles * rows * kTileLd * 4;
     off = (off + 15) & ~(size_t)15;
-    if (!gphi) off += ntiles * rows * kTileLd * (fp64 ? 8 : 4);
+    if (!gphi) off += (nphi > 0 ? nphi : ntiles) * rows * kTileLd * (fp64 ? 8 : 4);
     off = (off + 15) & ~(size_t)15;
     off += 2 * (size_t)sub * (D + 1) * (fp64 ? sizeof(Rec64) : sizeof(Rec32));
     off = (off + 15) & ~(size_t)15;
@@ -267,14 +281,18 @@ cudaError_t launch_fwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
     a.n_paths = b.n_paths;
     a.sub = std::max(1, tn.sub);
     const int warps = std::max(1, std::min(8, tn.warps));
-    // private tiles when the per-warp X and phi tiles stay small
-    a.ntiles = (!fp64 && tn.priv && fwd_smem_bytes(F, a.sub, b.D, false, warps) <= 100 * 1024) ? warps : 1;
+    // tn.priv 1: each warp its own 32 samples and tiles, when they stay small;
+    // 2: the warps share 32 samples, split the paths, a phi tile each; 0: the
+    // warps share 32 samples and one phi tile (shared-memory atomics)
+    a.ntiles = (!fp64 && tn.priv == 1 && fwd_smem_bytes(F, a.sub, b.D, false, warps) <= 100 * 1024) ? warps : 1;
     a.group = (!fp64 && M <= kFewRows) ? (int)(32 / M) : 0;
     if (a.group) a.ntiles = 1;
+    a.nphi = (!fp64 && !a.group && tn.priv == 2 && warps > 1 &&
+              fwd_smem_bytes(F, a.sub, b.D, false, 1, false, warps) <= 100 * 1024) ? warps : a.ntiles;
     // wide inputs: stage fewer paths at a time, and (FP64) drop the accumulator
     // tile for direct FP64 atomics into phi, until the block fits shared memory
     a.gphi = 0;
-    while (a.sub > 1 && fwd_smem_bytes(F, a.sub, b.D, fp64, a.ntiles) > kSmemMax) a.sub /= 2;
+    while (a.sub > 1 && fwd_smem_bytes(F, a.sub, b.D, fp64, a.ntiles, false, a.nphi) > kSmemMax) a.sub /= 2;
     if (fp64 && fwd_smem_bytes(F, a.sub, b.D, fp64, a.ntiles) > kSmemMax) {
         a.gphi = 1;
         a.sub = std::max(1, tn.sub);
@@ -294,7 +312,7 @@ cudaError_t launch_fwd_bucket(const qts_ensemble* e, const Bucket& b, const floa
     const int64_t chunks = (b.n_paths + a.paths_per_block - 1) / a.paths_per_block;
     const int64_t blocks = chunks * a.n_tiles;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const size_t smem = fwd_smem_bytes(F, a.sub, b.D, fp64, a.ntiles, a.gphi != 0);
+    const size_t smem = fwd_smem_bytes(F, a.sub, b.D, fp64, a.ntiles, a.gphi != 0, a.nphi);
     if (smem > kSmemMax) return cudaErrorInvalidConfiguration;
     // nodes per register pass: the tuned count, halved until it divides the rule's
     // padded node count (every smaller power of two then divides it too)

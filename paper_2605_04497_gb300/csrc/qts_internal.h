@@ -141,7 +141,9 @@ struct Tune {
     int sub = 32;         // paths per staged sub-chunk
     int np = 8;           // nodes per register pass (8, 4 or 2)
     int bpaths = 128;     // paths per work item of the fused forward + adjoint pass
-    int priv = 1;         // forward: let each warp own a sample tile when it fits
+    int priv = 1;         // forward: 1 each warp owns a sample tile (when it fits), 2 the
+                          // warps share one and split the paths with a phi tile each,
+                          // 0 they share one phi tile (shared-memory atomics)
     // choices of the batched-launch tuner (0: not tuned, the launch's default)
     int bt_paths = 0;     // paths per work item of the persistent batched kernel
     int bt_mode = 0;      // sample mapping of the packed fused pass: 2 (64 samples

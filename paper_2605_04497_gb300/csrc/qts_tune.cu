@@ -157,7 +157,7 @@ extern "C" qts_status qts_autotune(qts_ensemble* e, const float* X, int64_t M, i
             for (int warps : {2, 4, 8}) {
                 for (int paths : {128, 512, 2048}) {
                     for (int sub : {16, 32}) {
-                      for (int priv : {1, 0}) {
+                      for (int priv : {1, 2, 0}) {
                         Tune t = best;
                         t.np = np;
                         t.warps = warps;
