@@ -148,7 +148,7 @@ __device__ __forceinline__ bool stream_chunks(const Rec* __restrict__ rec, int64
                                               int* s_flag, int* status, Visit&& visit) {
     const int nsub = (int)((p1 - p0 + sub - 1) / sub);
     // phase_base[k] counts completed phases of barrier k before this call, so
-    // the driver can be called repeatedly (persistent kernels) on the same bars
+    // this routine can be called repeatedly (persistent kernels) on the same bars
     auto issue = [&](int c) {
         const int64_t q0 = p0 + (int64_t)c * sub;
         const int cnt = (int)imin64(sub, p1 - q0);
