@@ -67,9 +67,9 @@ typedef enum qts_status {
 /* n_quad = QTS_NQ_EXACT: per bucket of paths with at most w unique features,
    the fewest Gauss-Legendre points that make an order-s quantity exact,
    ceil((w - s + 1) / 2) (Thm 2; qts_exact_nodes).  The first-order, adjoint and
-   batched calls choose it per bucket, so short paths take fewer points than
-   long ones; the interaction and depth-first calls choose it once, from the
-   ensemble's widest path.  Unlike a fixed n_quad it is exact for every width
+   batched calls and pairwise interactions choose it per bucket, so short
+   paths take fewer points than long ones; interactions of order >= 3 and the
+   depth-first call choose it once, from the ensemble's widest path.  Unlike a fixed n_quad it is exact for every width
    up to QTS_MAX_UNIQUE_FEATURES_PER_PATH (32 points at width 64). */
 #define QTS_NQ_EXACT 0
 #define QTS_MAX_FEATURES_ORDER3 128
@@ -204,8 +204,9 @@ qts_status qts_shap_values_alg1(qts_ensemble *ens, const float *X, int64_t M, in
  * sibling-pair tables of qts_shap_values (each pair's element is one more
  * linear factor of every pair term; built by the first call that needs them,
  * so that call must not be inside a stream capture).  n_quad as
- * qts_shap_values; QTS_NQ_EXACT takes ceil((d - 1) / 2) points for the
- * ensemble's widest path d.
+ * qts_shap_values; QTS_NQ_EXACT takes ceil(D / 2) points per bucket of width
+ * D (the pair terms need ceil((D - 1) / 2), the diagonal's first-order values
+ * ceil(D / 2)).
  */
 qts_status qts_shap_interactions(qts_ensemble *ens, const float *X, int64_t M, int32_t F,
                                  int32_t n_quad, float *phi_ij, qts_stream_t stream);

@@ -51,8 +51,11 @@ struct IntArgs {
     QuadF q;
 };
 
+// the widest register pass a width takes (nodes per pass)
+__host__ __device__ constexpr int int_max_np(int D) { return D <= 6 ? 8 : (D <= 12 ? 4 : 2); }
+
 template <int D>
-cudaError_t launch_int_d(const IntArgs& a, bool pair_smem, int warps, int64_t blocks, size_t smem,
+cudaError_t launch_int_d(const IntArgs& a, int np, bool pair_smem, int warps, int64_t blocks, size_t smem,
                          cudaStream_t st);
 
 #if QTS_DEVICE_PARTS
@@ -250,16 +253,24 @@ static cudaError_t launch_int_t(const IntArgs& a, int warps, int64_t blocks, siz
     return cudaGetLastError();
 }
 
+// np: nodes per register pass, int_max_np(D), or 4 for widths up to 6 (a
+// rule of four points)
 template <int D>
-cudaError_t launch_int_d(const IntArgs& a, bool pair_smem, int warps, int64_t blocks, size_t smem,
-                                cudaStream_t st) {
-    constexpr int NP = D <= 6 ? 8 : (D <= 12 ? 4 : 2);
+cudaError_t launch_int_d(const IntArgs& a, int np, bool pair_smem, int warps, int64_t blocks, size_t smem,
+                         cudaStream_t st) {
+    constexpr int NP = int_max_np(D);
+    if constexpr (NP == 8) {
+        if (np < NP) {
+            if (pair_smem) return launch_int_t<D, NP / 2, true>(a, warps, blocks, smem, st);
+            return launch_int_t<D, NP / 2, false>(a, warps, blocks, smem, st);
+        }
+    }
     if (pair_smem) return launch_int_t<D, NP, true>(a, warps, blocks, smem, st);
     return launch_int_t<D, NP, false>(a, warps, blocks, smem, st);
 }
 
 #define QTS_INST(DD) \
-    template cudaError_t launch_int_d<DD>(const IntArgs&, bool, int, int64_t, size_t, cudaStream_t);
+    template cudaError_t launch_int_d<DD>(const IntArgs&, int, bool, int, int64_t, size_t, cudaStream_t);
 #if QTS_IN_PART(1)
 QTS_INST(32)
 #endif
@@ -354,9 +365,13 @@ cudaError_t launch_int_bucket(const qts_ensemble* e, const Bucket& b, bool pairs
     const int64_t blocks = chunks * a.n_tiles;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const int warps = 4;
+    // nodes per register pass: the width's widest, or half of it when that
+    // does not divide the rule's padded node count
+    const int np = q.n_pad % int_max_np(b.D) == 0 ? int_max_np(b.D) : int_max_np(b.D) / 2;
+    if (q.n_pad % np != 0) return cudaErrorInvalidValue;
     switch (b.D) {
 #define QTS_CASE(DD) \
-    case DD: return launch_int_d<DD>(a, pair_smem, warps, blocks, smem, st);
+    case DD: return launch_int_d<DD>(a, np, pair_smem, warps, blocks, smem, st);
         QTS_CASE(1) QTS_CASE(2) QTS_CASE(3) QTS_CASE(4) QTS_CASE(5) QTS_CASE(6) QTS_CASE(7)
         QTS_CASE(8) QTS_CASE(9) QTS_CASE(10) QTS_CASE(11) QTS_CASE(12) QTS_CASE(13) QTS_CASE(14)
         QTS_CASE(15) QTS_CASE(16) QTS_CASE(20) QTS_CASE(24) QTS_CASE(28) QTS_CASE(32)
@@ -388,9 +403,7 @@ extern "C" qts_status qts_shap_interactions(qts_ensemble* e, const float* X, int
     if (e->prep.max_unique > 32)
         return fail(QTS_ERR_UNSUPPORTED, "interactions support paths of at most 32 unique features");
     cudaStream_t s = (cudaStream_t)stream;
-    QuadF qf;  // QTS_NQ_EXACT: exact for the ensemble's widest path (order 2, Thm 2)
-    if (!make_quad(nodes_for(n_quad, e->prep.max_unique, 2), &qf, nullptr))
-        return fail(QTS_ERR_ARG, "quadrature rule");
+    if (n_quad != QTS_NQ_EXACT && (n_quad < 1 || n_quad > QTS_MAX_QUAD)) return fail(QTS_ERR_ARG, "quadrature rule");
     // the sibling-pair tables (built on the first call that needs them)
     st = ensure_batch_tables(e);
     if (st != QTS_OK) return st;
@@ -403,6 +416,13 @@ extern "C" qts_status qts_shap_interactions(qts_ensemble* e, const float* X, int
     cudaError_t ce = cudaMemsetAsync(e->d_work, 0, bytes, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "workspace clear");
     for (const Bucket& b : e->bprep.buckets) {
+        // the bucket's rule, padded to 4 nodes up to width 12 (a pass of 4 or 8
+        // nodes) and to 2 above.  QTS_NQ_EXACT: the pair terms need
+        // ceil((D - 1) / 2) points, but the diagonal holds first-order values,
+        // so the kernel takes the first-order count ceil(D / 2) (Thm 2)
+        QuadF qf;
+        if (!make_quad(nodes_for(n_quad, b.D, 1), &qf, nullptr, b.D <= 12 ? 4 : 2))
+            return fail(QTS_ERR_ARG, "quadrature rule");
         ce = launch_int_bucket(e, b, true, X, M, F, qf, acc_pair, acc_phi, s);
         if (ce != cudaSuccess) return cuda_fail(ce, "interaction kernel launch");
     }
@@ -506,8 +526,10 @@ extern "C" qts_status qts_shap_interactions_noalloc(qts_ensemble* e, const float
                         " accumulator doubles; the fixed scratch holds " + std::to_string(kNoAllocDoubles) +
                         " (use qts_shap_interactions for larger calls)");
     cudaStream_t s = (cudaStream_t)stream;
-    QuadF qf;  // QTS_NQ_EXACT: exact for the ensemble's widest path (order 2, Thm 2)
-    if (!make_quad(nodes_for(n_quad, e->prep.max_unique, 2), &qf, nullptr))
+    // QTS_NQ_EXACT: exact for the ensemble's widest path; first-order count,
+    // because the diagonal holds first-order values (Thm 2)
+    QuadF qf;
+    if (!make_quad(nodes_for(n_quad, e->prep.max_unique, 1), &qf, nullptr))
         return fail(QTS_ERR_ARG, "quadrature rule");
     void* scratch = nullptr;
     st = noalloc_scratch(&scratch);

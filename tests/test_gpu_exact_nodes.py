@@ -151,11 +151,22 @@ def test_odd_point_count(qts):
     fo = tiny_ensemble(8832, n_trees=6, depth=7, F=6, n_train=2000)
     Xf = synth.normal(8832, synth.STREAM_X, (40, 6))
     _batched(qts, [(ens, X, G), (fo, Xf, None)], 5)
+    # pairwise with 5 points (padded to 8 for widths up to 12)
+    E = qts.Ensemble.from_arrays(ens)
+    pairs = qts.shap_interactions(E, _cuda(X), 5).cpu().numpy().astype(np.float64)
+    E.sync_status()
+    E.close()
+    sii, phi = oracle.sii_exact(ens, X)
+    ref = oracle.interaction_matrix(sii, phi)
+    scale = np.maximum(np.abs(phi.sum(1)), np.abs(phi[:, :-1]).max(1))
+    assert (np.abs(pairs - ref).reshape(len(X), -1).max(1) / scale).max() <= TOL32
 
 
 def test_exact_interactions_and_depth_first(qts):
-    """Pairwise, third-order and Algorithm 1 take the rule of the ensemble's
-    widest path (orders 2, 3 and 1)."""
+    """Pairwise interactions take a rule per bucket (ceil(D / 2) points: the
+    diagonal holds first-order values; padded to 4, a 4-node pass for widths up
+    to 6); third order and Algorithm 1 take the rule of the ensemble's widest
+    path (orders 3 and 1).  Widths up to 12, odd ones included."""
     ens = tiny_ensemble(8841, n_trees=6, depth=12, F=14, n_train=4000)
     X = synth.normal(8841, synth.STREAM_X, (35, 14))
     E = qts.Ensemble.from_arrays(ens)
