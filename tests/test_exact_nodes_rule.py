@@ -90,3 +90,20 @@ def test_full_degree_path(qts, d):
     scale = np.abs(ref).max()
     assert np.abs(oracle.shap_quad(ens, X, n) - ref).max() <= 1e-13 * scale
     assert np.abs(oracle.shap_quad(ens, X, n - 1) - ref).max() > 1e-8 * scale
+
+
+@pytest.mark.parametrize("d", [5, 7, 9])
+def test_pairwise_diagonal_needs_the_first_order_count(qts, d):
+    """On a full-degree path of odd width d, ceil((d - 1) / 2) points make the
+    pair terms exact (Algorithm 1 with s = 2 against the exact expansion) but
+    not the first-order values the interaction matrix's diagonal holds, which
+    need ceil(d / 2): the pairwise call's rule is the first-order count."""
+    ens = _skewed_chain(d, d)
+    x = np.ones((1, d), np.float32)
+    sii, phi = oracle.sii_exact(ens, x)
+    n2, n1 = qts.exact_nodes(d, 2), qts.exact_nodes(d, 1)
+    assert n1 == n2 + 1
+    scale = np.abs(phi).max()
+    assert np.abs(oracle.alg1(ens, x, 2, n2) - sii[0]).max() <= 1e-13 * scale
+    assert np.abs(oracle.shap_quad(ens, x, n2) - phi).max() > 1e-8 * scale
+    assert np.abs(oracle.shap_quad(ens, x, n1) - phi).max() <= 1e-13 * scale
